@@ -1,0 +1,163 @@
+"""Pins of the oracle's iteration (Algorithm 1) and of its warp / MSD."""
+import numpy as np
+import pytest
+
+from oracle import mesh, register
+from paper_1411_2141_gb300 import inputs
+
+MODES = [("S0", "G0", "Q0"), ("S0", "G1", "Q0"), ("S1", "G0", "Q0"), ("S1", "G1", "Q0"),
+         ("S2", "G0", "Q0"), ("S2", "G1", "Q0"), ("S2", "G1", "Q1")]
+
+
+@pytest.fixture(scope="module")
+def small():
+    return inputs.make_case(inputs.CaseSpec(side=48, n_nodes=220, seed=11, dmax=2.0))
+
+
+@pytest.mark.parametrize("mode,grad,quad", MODES)
+def test_zero_force_on_identical_images(small, mode, grad, quad):
+    pb = register.Problem(small.V, small.T, small.Re, small.Re, 0.1, 1.0, mode, grad, quad)
+    u = np.zeros((pb.n, 2))
+    f, r, g = pb.sample(u)
+    assert np.abs(r).max() == 0.0
+    F = pb.force(u, f, r, g)
+    assert np.abs(F).max() == 0.0
+    u1, _ = pb.step(u)
+    assert np.abs(u1).max() < 1e-14
+
+
+@pytest.mark.parametrize("mode,quad", [("S0", "Q0"), ("S2", "Q0"), ("S2", "Q1")])
+def test_g1_force_is_gradient_of_data_energy(small, mode, quad):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, mode, "G1", quad)
+    rng = np.random.default_rng(0)
+    u = rng.uniform(-0.5, 0.5, size=(pb.n, 2))
+    f, r, g = pb.sample(u)
+    F = pb.force(u, f, r, g)
+    h = 1e-6
+    for i in rng.choice(pb.n, size=12, replace=False):
+        for d in range(2):
+            up = u.copy()
+            um = u.copy()
+            up[i, d] += h
+            um[i, d] -= h
+            fd = (pb.data_energy(up) - pb.data_energy(um)) / (2 * h)
+            assert abs(fd - F[i, d]) <= 1e-6 * max(1.0, abs(F[i, d])), (i, d, fd, F[i, d])
+
+
+@pytest.mark.parametrize("mode,grad,quad", MODES)
+def test_linear_ramp_closed_form_trajectory(small, mode, grad, quad):
+    """Te(x) = a.x + b0 and Re(x) = a.x + c: every node sees r = a.u + b0 - c
+    and grad = a, so u stays uniform and r_k = (1 - tau |a|^2)^k r_0."""
+    a = np.array([0.3, -0.2])
+    b0, c, tau = 0.9, 0.4, 1.0
+
+    def te(x, y):
+        return a[0] * x + a[1] * y + b0, np.full_like(x, a[0]), np.full_like(x, a[1])
+
+    def re(x, y):
+        return a[0] * x + a[1] * y + c
+
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, tau, mode, grad, quad,
+                          te_sampler=te, re_sampler=re)
+    n = 10
+    u, _ = pb.run(n)
+    r0 = b0 - c
+    rn = (1 - tau * a @ a) ** n * r0
+    expect = -(r0 - rn) * a / (a @ a)
+    np.testing.assert_allclose(u, np.broadcast_to(expect, u.shape), rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("quad", ["Q0", "Q1"])
+def test_energy_decreases_for_fem_form(small, quad):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, "S2", "G1", quad)
+    u = np.zeros((pb.n, 2))
+    e_prev = pb.total_energy(u)
+    for _ in range(25):
+        u, _ = pb.step(u)
+        e = pb.total_energy(u)
+        assert e < e_prev
+        e_prev = e
+
+
+@pytest.mark.parametrize("mode,grad,quad", MODES)
+def test_msd_decreases_on_phantom(case0, mode, grad, quad):
+    pb = register.Problem(case0.V, case0.T, case0.Re, case0.Te, 0.1, 1.0, mode, grad, quad)
+    u, _ = pb.run(20)
+    assert pb.msd(u) < pb.msd(np.zeros_like(u))
+
+
+@pytest.mark.parametrize("mode", ["S1", "S2"])
+def test_solve_satisfies_the_linear_system(small, mode):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, mode, "G1", "Q0")
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-1, 1, (pb.n, 2))
+    F = rng.uniform(-1, 1, (pb.n, 2))
+    u1 = pb.update(u, F)
+    if mode == "S1":
+        A = (1 + pb.lam) * np.diag(pb.m) - pb.lam * pb.Wadj.toarray()
+        rhs = pb.m[:, None] * (u - pb.tau * F)
+    else:
+        M, K = mesh.p1_mass_stiffness(pb.V, pb.T)
+        A = (M + pb.lam * K).toarray()
+        rhs = M @ u - pb.tau * F
+    np.testing.assert_allclose(A @ u1, rhs, atol=1e-11 * np.abs(rhs).max())
+
+
+def test_warp_with_zero_displacement_is_the_template(small):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0)
+    u = np.zeros((pb.n, 2))
+    np.testing.assert_allclose(pb.warp(u), small.Te, atol=1e-11)
+    np.testing.assert_allclose(pb.msd(u), np.mean((small.Te.astype(float) - small.Re) ** 2), rtol=1e-12)
+
+
+def test_warp_by_integer_shift_reads_shifted_pixels(small):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0)
+    u = np.tile([[2.0, 1.0]], (pb.n, 1))
+    R = pb.warp(u)
+    np.testing.assert_allclose(R[:-1, :-2], small.Te[1:, 2:], atol=1e-11)
+
+
+def test_p1_interpolation_reproduces_affine_fields(small):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0)
+    B = np.array([[0.01, -0.02], [0.03, 0.005]])
+    t = np.array([0.4, -0.7])
+    u = pb.V @ B.T + t
+    ud = pb.dense_displacement(u)
+    ys, xs = np.mgrid[0:pb.H, 0:pb.W].astype(float)
+    X = np.stack([xs, ys], -1)
+    np.testing.assert_allclose(ud, X @ B.T + t, atol=1e-12)
+    ud = pb.dense_displacement(np.tile(t, (pb.n, 1)))
+    np.testing.assert_allclose(ud, np.broadcast_to(t, ud.shape), atol=1e-14)
+
+
+def test_point_location_against_exhaustive_search(small):
+    P = small.V.astype(np.float64)
+    T = small.T.astype(np.int64)
+    H, W = small.Re.shape
+    owner = register.locate_pixels(P, T, W, H, chunk=37)
+    assert (owner >= 0).all()
+    for y in range(0, H, 3):
+        for x in range(W):
+            px = np.full(len(T), float(x))
+            py = np.full(len(T), float(y))
+            a, b, c = T[:, 0], T[:, 1], T[:, 2]
+            inside = ((register.edge_side(P, a, b, px, py) >= 0)
+                      & (register.edge_side(P, b, c, px, py) >= 0)
+                      & (register.edge_side(P, c, a, px, py) >= 0))
+            assert owner[y, x] == np.flatnonzero(inside).min()
+    # the owner really contains the pixel: barycentric coordinates are >= 0
+    # and reproduce the pixel position
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    tri = T[owner.ravel()]
+    lam_pos = register.interpolate_p1(P, T, owner, P, W, H)
+    np.testing.assert_allclose(lam_pos[..., 0], xs, atol=1e-10)
+    np.testing.assert_allclose(lam_pos[..., 1], ys, atol=1e-10)
+    assert tri.shape[0] == H * W
+
+
+def test_generated_meshes_cover_the_image(case0):
+    owner = register.locate_pixels(case0.V, case0.T, 128, 128)
+    assert (owner >= 0).all()
+    A = mesh.signed_area(case0.V.astype(float), case0.T)
+    assert A.min() > 0
+    np.testing.assert_allclose(A.sum(), 127.0 * 127.0, rtol=1e-12)
