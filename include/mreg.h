@@ -1,0 +1,238 @@
+/*
+ * mreg.h -- C ABI of the GB300 (sm_103a) mesh-based image registration library.
+ *
+ * The library runs the per-iteration hot path of triangular-mesh image
+ * registration (Baghaie, Yu, D'souza, "Fast Mesh-Based Medical Image
+ * Registration", Sec. 2 and Algorithm 1) on one GPU:
+ *
+ *   a0  cubic B-spline prefilter of both images (abstract; Sec. 2.1:
+ *       "spline interpolation" of Re and Te)
+ *   a1  sampling of the template at the displaced nodes, residual and the
+ *       nodal SSD energy (Eq. 2-4)
+ *   a2  the force F = (Te(V+u) - Re) grad Te(V+u) (Eq. 6) with the mesh
+ *       gradient of Eq. 9-10 on the deformed mesh, or the analytic B-spline
+ *       gradient; atomics-free, node-centric assembly
+ *   a3  the update: explicit step + one umbrella smoothing pass (Eq. 5, 14),
+ *       or a semi-implicit step whose sparse SPD system (abstract: "a sparse
+ *       system of linear equations") is solved by Jacobi-preconditioned CG
+ *       to a stated FP64 residual
+ *   a4  the dense barycentric warp of the template and the MSD (Sec. 1,
+ *       Fig. 3, Table 1)
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an mreg_status; none throws or aborts.  On error
+ *     mreg_last_error() gives a message (thread-local, valid until the next
+ *     call on the same thread).  After any error except MREG_ERR_CUDA the
+ *     handle stays valid and unchanged by the failed call.
+ *   - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls documented "asynchronous" only enqueue work.
+ *   - Device pointers must belong to the handle's device; host pointers may be
+ *     pageable or pinned.  The library never keeps a caller pointer: inputs
+ *     are copied during the call (or on the stream, for device inputs), and
+ *     the caller owns every buffer it passes.
+ *   - Coordinates are in pixel units: pixel (row y, column x) is centred at
+ *     the point (x, y), so an image of W x H pixels spans [0,W-1] x [0,H-1].
+ *     Images are float32, row-major, x fastest, with a row stride in elements.
+ */
+#ifndef MREG_H
+#define MREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MREG_VERSION 1
+
+typedef enum {
+  MREG_OK = 0,
+  MREG_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad option value   */
+  MREG_ERR_BAD_MESH = 2,      /* index out of range, degenerate triangle,
+                                 node outside the image, mesh not covering
+                                 the image                                  */
+  MREG_ERR_SIZE_MISMATCH = 3, /* Re and Te differ in size (Sec. 2.1 requires
+                                 images of the same size)                   */
+  MREG_ERR_NONFINITE = 4,     /* NaN or Inf in an input image or vector     */
+  MREG_ERR_CUDA = 5,          /* a CUDA runtime call failed                 */
+  MREG_ERR_OOM = 6,           /* device allocation failed                   */
+  MREG_ERR_NOT_CONVERGED = 7, /* a CG solve stopped at its iteration cap    */
+  MREG_ERR_DEVICE_CHECK = 8   /* a bounded device-side wait gave up         */
+} mreg_status;
+
+/* Smoothing / update form (the third step of the loop of Algorithm 1). */
+enum {
+  /* S0: u <- ((1-l) I + l A^Lap)(u - tau F): Eq. 5 then Eq. 14, one pass.   */
+  MREG_MODE_EXPLICIT = 0,
+  /* S1: backward Euler of the diffusion of Eq. 7 with the umbrella Laplacian
+   * of Eq. 11-13, symmetrised by the valence matrix D_m = diag(m_i):
+   *   ((1+l) D_m - l W) u' = D_m (u - tau F),  W = 0/1 node adjacency.       */
+  MREG_MODE_UMBRELLA_IMPLICIT = 1,
+  /* S2: P1 finite elements on the undeformed mesh (E = D + alpha S, Eq. 1):
+   *   (M + l K) u' = M u - tau F_w, M = consistent mass, K = stiffness,
+   *   F_w = quadrature-weighted force.                                       */
+  MREG_MODE_FEM_IMPLICIT = 2
+};
+
+/* Source of grad Te(V+u) in Eq. 6. */
+enum {
+  MREG_GRAD_MESH = 0,    /* Eq. 9-10 on the deformed mesh (the paper's)     */
+  MREG_GRAD_SPLINE = 1   /* analytic derivative of the cubic B-spline       */
+};
+
+/* Quadrature of the data term (FEM form only). */
+enum {
+  MREG_QUAD_NODES = 0,          /* nodes, weight = lumped area A(V_a)/3     */
+  MREG_QUAD_EDGE_MIDPOINTS = 1  /* 3 edge midpoints per triangle, A_T/3 each;
+                                   needs MREG_GRAD_SPLINE                    */
+};
+
+typedef struct mreg_handle mreg_handle;
+
+/* Triangular mesh (V, T) of Sec. 2.1.  Host memory.
+ *   xy : n_nodes * 2 floats, node i at (xy[2i], xy[2i+1]), pixel units.
+ *   tri: n_tris * 3 int32 node indices, 0-based; clockwise triangles are
+ *        reoriented.  The triangles must cover the image domain.            */
+typedef struct {
+  int32_t n_nodes;
+  int32_t n_tris;
+  const float* xy;
+  const int32_t* tri;
+} mreg_mesh;
+
+/* Image: width x height float32 values, row stride in elements (>= width).
+ * on_device != 0: data is a device pointer on the handle's device.          */
+typedef struct {
+  int32_t width;
+  int32_t height;
+  int64_t row_stride;
+  const float* data;
+  int32_t on_device;
+} mreg_image;
+
+typedef struct {
+  int32_t mode;        /* MREG_MODE_*                       (default S0)    */
+  int32_t grad;        /* MREG_GRAD_*                       (default MESH)  */
+  int32_t quad;        /* MREG_QUAD_*                       (default NODES) */
+  int32_t pcg_maxit;   /* CG iteration cap per solve, <= 10000 (default 100) */
+  double lambda;       /* smoothing weight; < 0 means tau * alpha (default) */
+  double pcg_rtol;     /* stop when ||b - A u'||_2 <= rtol ||b||_2, residual
+                          formed in FP64, per component     (default 1e-7)  */
+  int32_t block_size;  /* threads per block of the iteration kernel (multiple of
+                          32, <= 512); 0 = 256                              */
+  int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
+} mreg_options;
+
+typedef struct {
+  int32_t iterations_done;     /* total iterations since create / reset     */
+  int32_t last_pcg_iters;      /* CG iterations of the last solve (S1/S2)    */
+  int32_t max_pcg_iters;       /* largest count since create / reset         */
+  int32_t not_converged;       /* solves that stopped at the cap             */
+  double last_rel_resid;       /* ||b - A u'|| / ||b|| (FP64) of the last
+                                  solve, max over x and y                    */
+  double last_energy;          /* data energy at the last sampled iterate    */
+  int32_t grid_blocks;         /* launch shape of the iteration kernel       */
+  int32_t block_size;
+  int32_t device_status;       /* raw device status bits (0 = clean)         */
+} mreg_stats_t;
+
+/* Fields readable with mreg_get_field (mainly for parity tests). */
+enum {
+  MREG_FIELD_U = 0,          /* n_nodes x 2 float: displacement u             */
+  MREG_FIELD_FORCE = 1,      /* n_nodes x 2 float: the force F (Eq. 6, weighted
+                                for S2) that the last iteration applied       */
+  MREG_FIELD_TE_NODES = 2,   /* n_nodes float: Te(V+u) at the current u (the
+                                sample the next iteration starts from)        */
+  MREG_FIELD_RE_NODES = 3,   /* n_nodes float: Re(V), fixed                   */
+  MREG_FIELD_COEF_RE = 4,    /* H x W float: B-spline coefficients of Re      */
+  MREG_FIELD_COEF_TE = 5,    /* H x W float: B-spline coefficients of Te      */
+  MREG_FIELD_PIXEL_TRI = 6,  /* H x W int32: owning triangle of each pixel    */
+  MREG_FIELD_ENERGY = 7,     /* n double: data energy of each iteration of the
+                                last mreg_step call                           */
+  MREG_FIELD_PCG_ITERS = 8,  /* n int32: CG iterations of each iteration of
+                                the last mreg_step call                       */
+  MREG_FIELD_PCG_RESID = 9   /* n double: final relative FP64 residual of each
+                                solve of the last mreg_step call              */
+};
+
+/* Fill *opts with the defaults listed in mreg_options. */
+mreg_status mreg_default_options(mreg_options* opts);
+
+/* Create a registration problem on the current CUDA device (Algorithm 1,
+ * "Inputs" and "Pre-Computation").
+ *   mesh   host mesh (V, T); validated (indices, orientation, area, nodes in
+ *          the image, coverage) and copied.
+ *   Re, Te reference and template images of the same size (Sec. 2.1), host
+ *          or device; copied.
+ *   alpha  regularisation weight of Eq. 1 (>= 0); tau step size of Eq. 5 (> 0).
+ *   opts   NULL for defaults.
+ *   stream stream for the set-up work; the call returns after it finished.
+ * Set-up builds, on the host: incident-triangle CSR, node-graph CSR, valences,
+ * the FEM matrices (S2); on the device: B-spline coefficients of Re and Te,
+ * Re at the nodes, the pixel -> triangle map, u = 0.
+ * Errors: INVALID_ARG, BAD_MESH, SIZE_MISMATCH, NONFINITE, CUDA, OOM.  On error
+ * *out is NULL and nothing is leaked.                                       */
+mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_image* Te,
+                        double alpha, double tau, const mreg_options* opts, void* stream,
+                        mreg_handle** out);
+
+/* Redo the device part of the set-up on the images already held by the
+ * handle: prefilter both images, Re at the nodes (and edge midpoints),
+ * pixel -> triangle map, u = 0, counters cleared.  Asynchronous.            */
+mreg_status mreg_reset(mreg_handle* h, void* stream);
+
+/* Run n_iters iterations of the loop body of Algorithm 1 (energy, gradient,
+ * step, smoothing/solve) in one persistent cooperative kernel.  n_iters >= 0.
+ * Asynchronous: CG caps and device-side wait failures are reported by
+ * mreg_stats / mreg_sync.                                                  */
+mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream);
+
+/* Dense warp (Sec. 1, Fig. 3): for every pixel x, u(x) = barycentric (P1)
+ * interpolation of the node displacements on the undeformed triangle that
+ * owns x; R(x) = Te(x + u(x)) by the cubic B-spline.  Asynchronous.
+ *   out_dev  device H x W float buffer (row stride W) for R, or NULL.
+ *   msd_dev  device double for MSD = mean over pixels of (R - Re)^2, or NULL. */
+mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* stream);
+
+/* MSD of the current displacement (abstract; Table 1), FP64.  Blocks until
+ * the value is on the host.                                                 */
+mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream);
+
+/* Data energy (Eq. 4; lumped or edge-midpoint weighted for S2) at the last
+ * iterate sampled by mreg_step.  Blocks.                                    */
+mreg_status mreg_energy(mreg_handle* h, double* out_host, void* stream);
+
+/* Copy u (n_nodes x 2 float, node order of the input mesh) out / in.
+ * dst_on_device / src_on_device select device or host memory.  get_u blocks
+ * when the destination is host memory; set_u is asynchronous for device
+ * sources and rejects non-finite host values (NONFINITE).                   */
+mreg_status mreg_get_u(mreg_handle* h, float* dst, int32_t dst_on_device, void* stream);
+mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, void* stream);
+
+/* Copy one of the MREG_FIELD_* arrays.  count_out (may be NULL) receives the
+ * number of elements; dst may be NULL to query the count only.  Blocks when
+ * dst is host memory.                                                       */
+mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst_on_device,
+                           int64_t* count_out, void* stream);
+
+/* Wait for the stream and report the solver / device state.  Returns
+ * MREG_ERR_DEVICE_CHECK if a bounded device wait gave up, else
+ * MREG_ERR_NOT_CONVERGED if a solve hit its cap since the last reset, else
+ * MREG_OK.  out may be NULL.                                                */
+mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream);
+
+/* Release every resource of the handle (after the handle's work finished).
+ * NULL is accepted.                                                         */
+void mreg_destroy(mreg_handle* h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* mreg_last_error(void);
+
+/* Library ABI version (MREG_VERSION). */
+int32_t mreg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MREG_H */

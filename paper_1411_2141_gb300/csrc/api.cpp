@@ -1,0 +1,776 @@
+// C ABI of the registration library (declared in include/mreg.h): argument
+// validation, the host-side mesh topology builder (Algorithm 1,
+// "Pre-Computation": 1-ring, neighbour triangles, operator matrices), the
+// device arena and the launch sequence of each entry point.
+#include "mreg.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mreg_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mreg_status fail(mreg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+mreg_status cuda_fail(cudaError_t e, const char* what) {
+  const mreg_status st = (e == cudaErrorMemoryAllocation) ? MREG_ERR_OOM : MREG_ERR_CUDA;
+  return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+  } while (0)
+
+constexpr int kHistCap = 4096;
+constexpr int kChunk = 4096;   // iterations per launch of the iteration kernel
+constexpr int kMaxPcgIt = 10000;
+constexpr double kDegenerateRel = 1e-12;
+
+// Host-side mesh data and operators, built once per mesh.
+struct HostMesh {
+  int nV = 0, nT = 0, nE = 0, nnz = 0;
+  std::vector<float> xy;
+  std::vector<int> tri;                   // counter-clockwise
+  std::vector<int> inc_ptr, inc_tri;      // incident triangles, ascending
+  std::vector<int> inc_opp;               // 2 per incidence: the other corners, CCW
+  std::vector<int> adj_ptr, adj_col, adj_edge;
+  std::vector<int> edges;                 // 2 per edge, a < b
+  std::vector<float> edge_w;              // sum over the edge's triangles of A_T / 3
+  std::vector<float> lumped;              // A(V_a) / 3
+  std::vector<float> Mdiag, Moff, Adiag, Aoff, dinv;
+  double area_floor = 0.0;
+};
+
+int find_in_row(const HostMesh& m, int i, int j) {
+  const int* b = m.adj_col.data() + m.adj_ptr[i];
+  const int* e = m.adj_col.data() + m.adj_ptr[i + 1];
+  const int* p = std::lower_bound(b, e, j);
+  return (p != e && *p == j) ? (int)(p - m.adj_col.data()) : -1;
+}
+
+mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m) {
+  m.nV = mesh->n_nodes;
+  m.nT = mesh->n_tris;
+  const int nV = m.nV, nT = m.nT;
+  m.xy.assign(mesh->xy, mesh->xy + 2 * (size_t)nV);
+  for (int i = 0; i < nV; ++i) {
+    const float x = m.xy[2 * i], y = m.xy[2 * i + 1];
+    if (!std::isfinite(x) || !std::isfinite(y))
+      return fail(MREG_ERR_NONFINITE, "node %d has a non-finite coordinate", i);
+    if (x < 0.0f || y < 0.0f || x > (float)(W - 1) || y > (float)(H - 1))
+      return fail(MREG_ERR_BAD_MESH, "node %d (%g, %g) lies outside the image [0,%d]x[0,%d]", i,
+                  (double)x, (double)y, W - 1, H - 1);
+  }
+  m.tri.assign(mesh->tri, mesh->tri + 3 * (size_t)nT);
+  std::vector<double> area(nT);
+  double total = 0.0;
+  for (int t = 0; t < nT; ++t) {
+    int* c = &m.tri[3 * (size_t)t];
+    for (int k = 0; k < 3; ++k)
+      if (c[k] < 0 || c[k] >= nV)
+        return fail(MREG_ERR_BAD_MESH, "triangle %d has node index %d out of range", t, c[k]);
+    if (c[0] == c[1] || c[1] == c[2] || c[0] == c[2])
+      return fail(MREG_ERR_BAD_MESH, "triangle %d repeats a node", t);
+    const double ax = m.xy[2 * c[0]], ay = m.xy[2 * c[0] + 1];
+    const double bx = m.xy[2 * c[1]], by = m.xy[2 * c[1] + 1];
+    const double cx = m.xy[2 * c[2]], cy = m.xy[2 * c[2] + 1];
+    double a2 = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    if (a2 < 0.0) {   // clockwise: reorient
+      std::swap(c[1], c[2]);
+      a2 = -a2;
+    }
+    area[t] = 0.5 * a2;
+    total += area[t];
+  }
+  const double mean = total / nT;
+  m.area_floor = kDegenerateRel * mean;
+  for (int t = 0; t < nT; ++t)
+    if (!(area[t] > m.area_floor))
+      return fail(MREG_ERR_BAD_MESH, "triangle %d is degenerate (area %g)", t, area[t]);
+  const double domain = (double)(W - 1) * (double)(H - 1);
+  if (std::fabs(total - domain) > 1e-6 * domain)
+    return fail(MREG_ERR_BAD_MESH,
+                "triangle areas sum to %.9g but the image domain has area %.9g: the mesh does "
+                "not tile the image",
+                total, domain);
+
+  // incident triangles of every node, ascending triangle index (Eq. 10)
+  m.inc_ptr.assign(nV + 1, 0);
+  for (int t = 0; t < nT; ++t)
+    for (int k = 0; k < 3; ++k) m.inc_ptr[m.tri[3 * (size_t)t + k] + 1]++;
+  for (int i = 0; i < nV; ++i) {
+    if (m.inc_ptr[i + 1] == 0) return fail(MREG_ERR_BAD_MESH, "node %d belongs to no triangle", i);
+    m.inc_ptr[i + 1] += m.inc_ptr[i];
+  }
+  m.inc_tri.assign(3 * (size_t)nT, 0);
+  m.inc_opp.assign(6 * (size_t)nT, 0);
+  {
+    std::vector<int> fill(m.inc_ptr.begin(), m.inc_ptr.end() - 1);
+    for (int t = 0; t < nT; ++t)
+      for (int k = 0; k < 3; ++k) {
+        const int pos = fill[m.tri[3 * (size_t)t + k]]++;
+        m.inc_tri[pos] = t;
+        m.inc_opp[2 * (size_t)pos] = m.tri[3 * (size_t)t + (k + 1) % 3];
+        m.inc_opp[2 * (size_t)pos + 1] = m.tri[3 * (size_t)t + (k + 2) % 3];
+      }
+  }
+
+  // node graph: the 1-ring N1(i) of Eq. 11, ascending
+  {
+    std::vector<std::vector<int>> nb(nV);
+    for (int t = 0; t < nT; ++t) {
+      const int a = m.tri[3 * (size_t)t], b = m.tri[3 * (size_t)t + 1], c = m.tri[3 * (size_t)t + 2];
+      nb[a].push_back(b), nb[a].push_back(c);
+      nb[b].push_back(a), nb[b].push_back(c);
+      nb[c].push_back(a), nb[c].push_back(b);
+    }
+    m.adj_ptr.assign(nV + 1, 0);
+    for (int i = 0; i < nV; ++i) {
+      std::sort(nb[i].begin(), nb[i].end());
+      nb[i].erase(std::unique(nb[i].begin(), nb[i].end()), nb[i].end());
+      m.adj_ptr[i + 1] = m.adj_ptr[i] + (int)nb[i].size();
+    }
+    m.nnz = m.adj_ptr[nV];
+    m.adj_col.resize(m.nnz);
+    for (int i = 0; i < nV; ++i) std::copy(nb[i].begin(), nb[i].end(), m.adj_col.begin() + m.adj_ptr[i]);
+  }
+  // unique edges (a < b) and the edge id of every adjacency entry
+  m.adj_edge.assign(m.nnz, -1);
+  m.edges.clear();
+  for (int i = 0; i < nV; ++i)
+    for (int k = m.adj_ptr[i]; k < m.adj_ptr[i + 1]; ++k)
+      if (m.adj_col[k] > i) {
+        m.adj_edge[k] = (int)(m.edges.size() / 2);
+        m.edges.push_back(i);
+        m.edges.push_back(m.adj_col[k]);
+      }
+  m.nE = (int)(m.edges.size() / 2);
+  for (int i = 0; i < nV; ++i)
+    for (int k = m.adj_ptr[i]; k < m.adj_ptr[i + 1]; ++k)
+      if (m.adj_col[k] < i) m.adj_edge[k] = m.adj_edge[find_in_row(m, m.adj_col[k], i)];
+
+  // quadrature weights and FEM operators on the undeformed mesh
+  std::vector<double> lumped(nV, 0.0), ew(m.nE, 0.0);
+  std::vector<double> Md(nV, 0.0), Kd(nV, 0.0), Mo(m.nnz, 0.0), Ko(m.nnz, 0.0);
+  for (int t = 0; t < nT; ++t) {
+    const int c[3] = {m.tri[3 * (size_t)t], m.tri[3 * (size_t)t + 1], m.tri[3 * (size_t)t + 2]};
+    const double A = area[t];
+    for (int k = 0; k < 3; ++k) {
+      lumped[c[k]] += A / 3.0;
+      const int a = c[k], b = c[(k + 1) % 3];
+      ew[m.adj_edge[find_in_row(m, a, b)]] += A / 3.0;
+    }
+    if (mode == MREG_MODE_FEM_IMPLICIT) {
+      // edge opposite corner k, oriented counter-clockwise: e_k = P_{k+2} - P_{k+1}
+      double ex[3], ey[3];
+      for (int k = 0; k < 3; ++k) {
+        const int p = c[(k + 1) % 3], q = c[(k + 2) % 3];
+        ex[k] = (double)m.xy[2 * q] - (double)m.xy[2 * p];
+        ey[k] = (double)m.xy[2 * q + 1] - (double)m.xy[2 * p + 1];
+      }
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) {
+          const double kxy = (ex[x] * ex[y] + ey[x] * ey[y]) / (4.0 * A);
+          const double mxy = (x == y) ? A / 6.0 : A / 12.0;
+          if (x == y) {
+            Md[c[x]] += mxy;
+            Kd[c[x]] += kxy;
+          } else {
+            const int pos = find_in_row(m, c[x], c[y]);
+            Mo[pos] += mxy;
+            Ko[pos] += kxy;
+          }
+        }
+    }
+  }
+  m.lumped.resize(nV);
+  for (int i = 0; i < nV; ++i) m.lumped[i] = (float)lumped[i];
+  m.edge_w.resize(m.nE);
+  for (int e = 0; e < m.nE; ++e) m.edge_w[e] = (float)ew[e];
+  m.dinv.assign(nV, 0.0f);
+  m.Mdiag.assign(nV, 0.0f);
+  m.Adiag.assign(nV, 0.0f);
+  m.Moff.assign(m.nnz, 0.0f);
+  m.Aoff.assign(m.nnz, 0.0f);
+  if (mode == MREG_MODE_UMBRELLA_IMPLICIT) {
+    for (int i = 0; i < nV; ++i)
+      m.dinv[i] = (float)(1.0 / ((1.0 + lam) * (double)(m.adj_ptr[i + 1] - m.adj_ptr[i])));
+  } else if (mode == MREG_MODE_FEM_IMPLICIT) {
+    for (int i = 0; i < nV; ++i) {
+      const double ad = Md[i] + lam * Kd[i];
+      m.Mdiag[i] = (float)Md[i];
+      m.Adiag[i] = (float)ad;
+      m.dinv[i] = (float)(1.0 / ad);
+    }
+    for (int k = 0; k < m.nnz; ++k) {
+      m.Moff[k] = (float)Mo[k];
+      m.Aoff[k] = (float)(Mo[k] + lam * Ko[k]);
+    }
+  }
+  return MREG_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct mreg_handle {
+  int dev = 0, num_sms = 0;
+  int W = 0, H = 0, nV = 0, nT = 0, nE = 0, nnz = 0;
+  mreg_options opts{};
+  double alpha = 0.0, tau = 0.0, lam = 0.0;
+  int form = 0, grad = 0;
+  int grid = 0, block = 0, warp_grid = 0;
+  float area_floor = 0.0f;
+  int iterations_done = 0, last_n_iters = 0, last_force_buf = 0;
+  void* arena = nullptr;
+  // device arrays
+  float *Re = nullptr, *Te = nullptr, *cRe = nullptr, *cTe = nullptr, *tmp = nullptr;
+  int* pix_tri = nullptr;
+  float2* V = nullptr;
+  int *tri = nullptr, *inc_ptr = nullptr;
+  int2* inc_opp = nullptr;
+  int *adj_ptr = nullptr, *adj_col = nullptr, *adj_edge = nullptr;
+  int2* edges = nullptr;
+  float *edge_w = nullptr, *lumped = nullptr, *Mdiag = nullptr, *Moff = nullptr, *Adiag = nullptr,
+        *Aoff = nullptr, *dinv = nullptr;
+  float *ReV = nullptr, *ReQ = nullptr, *f = nullptr;
+  float2 *u = nullptr, *F = nullptr, *u0 = nullptr, *hq = nullptr;
+  float2 *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *rt = nullptr;
+  float4* b = nullptr;
+  float* part = nullptr;
+  unsigned long long* bar = nullptr;
+  int* status = nullptr;
+  double* last = nullptr;
+  double* energy_hist = nullptr;
+  int* pcg_it_hist = nullptr;
+  double* pcg_res_hist = nullptr;
+  float* warp_part = nullptr;
+  double* msd = nullptr;
+  int* counters = nullptr;   // [0] uncovered pixels, [1] non-finite values
+
+  mreg::IterArgs iter_args(int n_iters, int it0) const {
+    mreg::IterArgs a{};
+    a.it0 = it0;
+    a.nV = nV;
+    a.nE = nE;
+    a.W = W;
+    a.H = H;
+    a.n_iters = n_iters;
+    a.maxit = opts.pcg_maxit;
+    a.hist_cap = kHistCap;
+    a.tau = (float)tau;
+    a.lam = (float)lam;
+    a.area_floor = area_floor;
+    a.rtol2 = (float)(opts.pcg_rtol * opts.pcg_rtol);
+    a.tau_ff = make_float2((float)tau, (float)(tau - (double)(float)tau));
+    a.lam_ff = make_float2((float)lam, (float)(lam - (double)(float)lam));
+    a.V = V;
+    a.inc_ptr = inc_ptr;
+    a.inc_opp = inc_opp;
+    a.adj_ptr = adj_ptr;
+    a.adj_col = adj_col;
+    a.adj_edge = adj_edge;
+    a.edges = edges;
+    a.edge_w = edge_w;
+    a.Mdiag = Mdiag;
+    a.Moff = Moff;
+    a.Adiag = Adiag;
+    a.Aoff = Aoff;
+    a.dinv = dinv;
+    a.lumped = lumped;
+    a.cTe = cTe;
+    a.ReV = ReV;
+    a.ReQ = ReQ;
+    a.u = u;
+    a.f = f;
+    a.F = F;
+    a.u0 = u0;
+    a.hq = hq;
+    a.r = r;
+    a.z = z;
+    a.p0 = p0;
+    a.p1 = p1;
+    a.q = q;
+    a.rt = rt;
+    a.b = b;
+    a.part = part;
+    a.bar = bar;
+    a.status = status;
+    a.energy_hist = energy_hist;
+    a.pcg_it_hist = pcg_it_hist;
+    a.pcg_res_hist = pcg_res_hist;
+    a.last = last;
+    return a;
+  }
+};
+
+namespace {
+
+mreg_status validate_image(const mreg_image* im, const char* name) {
+  if (!im) return fail(MREG_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!im->data) return fail(MREG_ERR_INVALID_ARG, "%s.data is NULL", name);
+  if (im->width < 2 || im->height < 2)
+    return fail(MREG_ERR_INVALID_ARG, "%s must be at least 2x2 pixels (got %dx%d)", name, im->width,
+                im->height);
+  if (im->row_stride < im->width)
+    return fail(MREG_ERR_INVALID_ARG, "%s.row_stride %lld < width %d", name,
+                (long long)im->row_stride, im->width);
+  if ((int64_t)im->width * im->height > (int64_t)INT32_MAX)
+    return fail(MREG_ERR_INVALID_ARG, "%s has more than 2^31 pixels", name);
+  if (!im->on_device) {
+    for (int64_t y = 0; y < im->height; ++y) {
+      const float* row = im->data + y * im->row_stride;
+      for (int64_t x = 0; x < im->width; ++x)
+        if (!std::isfinite(row[x]))
+          return fail(MREG_ERR_NONFINITE, "%s has a non-finite value at (%lld, %lld)", name,
+                      (long long)x, (long long)y);
+    }
+  }
+  return MREG_OK;
+}
+
+// Copy an image into a dense device buffer (device images are checked for
+// finiteness on the device first).
+mreg_status upload_image(mreg_handle* h, const mreg_image* im, float* dst, cudaStream_t s,
+                         const char* name) {
+  const size_t W = (size_t)im->width, H = (size_t)im->height;
+  if (!im->on_device) {   // host images were checked for finiteness before any CUDA call
+    CK(cudaMemcpy2DAsync(dst, W * sizeof(float), im->data, (size_t)im->row_stride * sizeof(float),
+                         W * sizeof(float), H, cudaMemcpyHostToDevice, s),
+       "image upload");
+  } else {
+    CK(cudaMemsetAsync(h->counters + 1, 0, sizeof(int), s), "memset");
+    CK(mreg::launch_count_nonfinite(im->data, (int)W, (int)H, im->row_stride, h->counters + 1, s),
+       "non-finite check");
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (bad) return fail(MREG_ERR_NONFINITE, "%s has %d non-finite values", name, bad);
+    CK(cudaMemcpy2DAsync(dst, W * sizeof(float), im->data, (size_t)im->row_stride * sizeof(float),
+                         W * sizeof(float), H, cudaMemcpyDeviceToDevice, s),
+       "image copy");
+  }
+  return MREG_OK;
+}
+
+mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
+  CK(mreg::launch_prefilter(h->Re, h->W, h->tmp, h->cRe, h->W, h->H, s), "prefilter Re");
+  CK(mreg::launch_prefilter(h->Te, h->W, h->tmp, h->cTe, h->W, h->H, s), "prefilter Te");
+  CK(mreg::launch_sample_nodes(h->cRe, h->W, h->H, h->V, h->nV, h->ReV, s), "Re at nodes");
+  if (h->form == mreg::kFormFemEdges)
+    CK(mreg::launch_sample_edges(h->cRe, h->W, h->H, h->V, h->edges, h->nE, h->ReQ, s),
+       "Re at edge midpoints");
+  CK(cudaMemsetAsync(h->counters, 0, sizeof(int), s), "memset");
+  CK(mreg::launch_pixel_map(h->V, h->tri, h->nT, h->W, h->H, h->pix_tri,
+                            check_cover ? h->counters : nullptr, s),
+     "pixel map");
+  CK(cudaMemsetAsync(h->u, 0, sizeof(float2) * h->nV, s), "memset u");
+  CK(cudaMemsetAsync(h->F, 0, 2 * sizeof(float2) * h->nV, s), "memset F");
+  CK(cudaMemsetAsync(h->f, 0, sizeof(float) * h->nV, s), "memset f");
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), s), "memset status");
+  CK(cudaMemsetAsync(h->last, 0, sizeof(double) * 8, s), "memset stats");
+  h->iterations_done = 0;
+  h->last_n_iters = 0;
+  h->last_force_buf = 0;
+  if (check_cover) {
+    int unc = 0;
+    CK(cudaMemcpyAsync(&unc, h->counters, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (unc) return fail(MREG_ERR_BAD_MESH, "%d pixel centres are not inside any triangle", unc);
+  }
+  return MREG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mreg_status mreg_default_options(mreg_options* o) {
+  if (!o) return fail(MREG_ERR_INVALID_ARG, "options pointer is NULL");
+  std::memset(o, 0, sizeof *o);
+  o->mode = MREG_MODE_EXPLICIT;
+  o->grad = MREG_GRAD_MESH;
+  o->quad = MREG_QUAD_NODES;
+  o->pcg_maxit = 100;
+  o->lambda = -1.0;
+  o->pcg_rtol = 1e-7;
+  o->block_size = 0;
+  o->grid_blocks = 0;
+  return MREG_OK;
+}
+
+mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_image* Te,
+                        double alpha, double tau, const mreg_options* opts, void* stream,
+                        mreg_handle** out) {
+  if (!out) return fail(MREG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !mesh->xy || !mesh->tri) return fail(MREG_ERR_INVALID_ARG, "mesh or its arrays are NULL");
+  if (mesh->n_nodes < 3 || mesh->n_tris < 1)
+    return fail(MREG_ERR_INVALID_ARG, "mesh needs >= 3 nodes and >= 1 triangle");
+  mreg_status st = validate_image(Re, "Re");
+  if (st) return st;
+  st = validate_image(Te, "Te");
+  if (st) return st;
+  if (Re->width != Te->width || Re->height != Te->height)
+    return fail(MREG_ERR_SIZE_MISMATCH, "Re is %dx%d but Te is %dx%d", Re->width, Re->height,
+                Te->width, Te->height);
+  if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(MREG_ERR_INVALID_ARG, "alpha must be >= 0");
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(MREG_ERR_INVALID_ARG, "tau must be > 0");
+  mreg_options o;
+  mreg_default_options(&o);
+  if (opts) o = *opts;
+  if (o.mode < 0 || o.mode > 2) return fail(MREG_ERR_INVALID_ARG, "unknown mode %d", o.mode);
+  if (o.grad < 0 || o.grad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown grad %d", o.grad);
+  if (o.quad < 0 || o.quad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown quad %d", o.quad);
+  if (o.quad == MREG_QUAD_EDGE_MIDPOINTS &&
+      (o.mode != MREG_MODE_FEM_IMPLICIT || o.grad != MREG_GRAD_SPLINE))
+    return fail(MREG_ERR_INVALID_ARG, "edge-midpoint quadrature needs the FEM mode and the spline gradient");
+  if (!(o.pcg_rtol > 0.0) || !(o.pcg_rtol < 1.0)) return fail(MREG_ERR_INVALID_ARG, "pcg_rtol must be in (0,1)");
+  if (o.pcg_maxit < 1 || o.pcg_maxit > kMaxPcgIt)
+    return fail(MREG_ERR_INVALID_ARG, "pcg_maxit must be in [1, %d]", kMaxPcgIt);
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 512 || o.block_size % 32))
+    return fail(MREG_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
+  if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
+  const double lam = o.lambda < 0.0 ? tau * alpha : o.lambda;
+  if (!std::isfinite(lam)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
+
+  const int W = Re->width, H = Re->height;
+  HostMesh hm;
+  try {
+    st = build_mesh(mesh, W, H, o.mode, lam, hm);
+  } catch (const std::bad_alloc&) {
+    return fail(MREG_ERR_OOM, "host allocation failed while building the mesh topology");
+  }
+  if (st) return st;
+
+  mreg_handle* h = new (std::nothrow) mreg_handle();
+  if (!h) return fail(MREG_ERR_OOM, "host allocation failed");
+  struct Guard {
+    mreg_handle*& h;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) mreg_destroy(h);
+    }
+  } guard{h};
+
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaGetDevice(&h->dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev), "attribute");
+  h->W = W;
+  h->H = H;
+  h->nV = hm.nV;
+  h->nT = hm.nT;
+  h->nE = hm.nE;
+  h->nnz = hm.nnz;
+  h->opts = o;
+  h->alpha = alpha;
+  h->tau = tau;
+  h->lam = lam;
+  h->grad = o.grad;
+  h->form = o.mode == MREG_MODE_EXPLICIT ? mreg::kFormExplicit
+            : o.mode == MREG_MODE_UMBRELLA_IMPLICIT
+                ? mreg::kFormUmbrella
+                : (o.quad == MREG_QUAD_EDGE_MIDPOINTS ? mreg::kFormFemEdges : mreg::kFormFemNodes);
+  h->area_floor = (float)hm.area_floor;
+
+  // launch shape of the iteration kernel
+  h->block = o.block_size ? o.block_size : 256;
+  int per_sm = 0;
+  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, &per_sm), "occupancy");
+  if (per_sm < 1) return fail(MREG_ERR_INVALID_ARG, "block_size %d does not fit on an SM", h->block);
+  const int max_grid = per_sm * h->num_sms;
+  const int want = (h->nV + h->block - 1) / h->block;
+  h->grid = o.grid_blocks ? o.grid_blocks : std::max(1, std::min(want, max_grid));
+  if (h->grid > max_grid)
+    return fail(MREG_ERR_INVALID_ARG, "grid_blocks %d exceeds the %d co-resident blocks", h->grid,
+                max_grid);
+  h->warp_grid = mreg::warp_grid_blocks(W, H, h->num_sms);
+
+  // one arena for every device array
+  const size_t npx = (size_t)W * H, nV = hm.nV, nT = hm.nT, nE = std::max(hm.nE, 1),
+               nnz = std::max(hm.nnz, 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off += align_up(bytes);
+    return o2;
+  };
+  const size_t o_Re = take(npx * 4), o_Te = take(npx * 4), o_cRe = take(npx * 4),
+               o_cTe = take(npx * 4), o_tmp = take(npx * 4), o_pix = take(npx * 4),
+               o_V = take(nV * 8), o_tri = take(nT * 12), o_incp = take((nV + 1) * 4),
+               o_inct = take(nT * 24), o_adjp = take((nV + 1) * 4), o_adjc = take(nnz * 4),
+               o_adje = take(nnz * 4), o_edges = take(nE * 8), o_ew = take(nE * 4),
+               o_lump = take(nV * 4), o_Md = take(nV * 4), o_Mo = take(nnz * 4),
+               o_Ad = take(nV * 4), o_Ao = take(nnz * 4), o_dinv = take(nV * 4),
+               o_ReV = take(nV * 4), o_ReQ = take(nE * 4), o_f = take(nV * 4), o_u = take(nV * 8),
+               o_F = take(2 * nV * 8), o_u0 = take(2 * nV * 8), o_hq = take(nE * 8),
+               o_r = take(nV * 8), o_z = take(nV * 8), o_p0 = take(nV * 8), o_p1 = take(nV * 8),
+               o_q = take(nV * 8), o_rt = take(nV * 8), o_b = take(nV * 16),
+               o_part = take((size_t)2 * h->grid * mreg::kRec * 4), o_bar = take(8),
+               o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
+               o_ih = take(kHistCap * 4), o_rh = take(kHistCap * 8),
+               o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16);
+  CK(cudaMalloc(&h->arena, off), "device allocation");
+  char* base = (char*)h->arena;
+  h->Re = (float*)(base + o_Re);
+  h->Te = (float*)(base + o_Te);
+  h->cRe = (float*)(base + o_cRe);
+  h->cTe = (float*)(base + o_cTe);
+  h->tmp = (float*)(base + o_tmp);
+  h->pix_tri = (int*)(base + o_pix);
+  h->V = (float2*)(base + o_V);
+  h->tri = (int*)(base + o_tri);
+  h->inc_ptr = (int*)(base + o_incp);
+  h->inc_opp = (int2*)(base + o_inct);
+  h->adj_ptr = (int*)(base + o_adjp);
+  h->adj_col = (int*)(base + o_adjc);
+  h->adj_edge = (int*)(base + o_adje);
+  h->edges = (int2*)(base + o_edges);
+  h->edge_w = (float*)(base + o_ew);
+  h->lumped = (float*)(base + o_lump);
+  h->Mdiag = (float*)(base + o_Md);
+  h->Moff = (float*)(base + o_Mo);
+  h->Adiag = (float*)(base + o_Ad);
+  h->Aoff = (float*)(base + o_Ao);
+  h->dinv = (float*)(base + o_dinv);
+  h->ReV = (float*)(base + o_ReV);
+  h->ReQ = (float*)(base + o_ReQ);
+  h->f = (float*)(base + o_f);
+  h->u = (float2*)(base + o_u);
+  h->F = (float2*)(base + o_F);
+  h->u0 = (float2*)(base + o_u0);
+  h->hq = (float2*)(base + o_hq);
+  h->r = (float2*)(base + o_r);
+  h->z = (float2*)(base + o_z);
+  h->p0 = (float2*)(base + o_p0);
+  h->p1 = (float2*)(base + o_p1);
+  h->q = (float2*)(base + o_q);
+  h->rt = (float2*)(base + o_rt);
+  h->b = (float4*)(base + o_b);
+  h->part = (float*)(base + o_part);
+  h->bar = (unsigned long long*)(base + o_bar);
+  h->status = (int*)(base + o_status);
+  h->last = (double*)(base + o_last);
+  h->energy_hist = (double*)(base + o_eh);
+  h->pcg_it_hist = (int*)(base + o_ih);
+  h->pcg_res_hist = (double*)(base + o_rh);
+  h->warp_part = (float*)(base + o_wp);
+  h->msd = (double*)(base + o_msd);
+  h->counters = (int*)(base + o_cnt);
+
+  st = upload_image(h, Re, h->Re, s, "Re");
+  if (st) return st;
+  st = upload_image(h, Te, h->Te, s, "Te");
+  if (st) return st;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  CK(up(h->V, hm.xy.data(), nV * 8), "upload");
+  CK(up(h->tri, hm.tri.data(), nT * 12), "upload");
+  CK(up(h->inc_ptr, hm.inc_ptr.data(), (nV + 1) * 4), "upload");
+  CK(up(h->inc_opp, hm.inc_opp.data(), nT * 24), "upload");
+  CK(up(h->adj_ptr, hm.adj_ptr.data(), (nV + 1) * 4), "upload");
+  CK(up(h->adj_col, hm.adj_col.data(), (size_t)hm.nnz * 4), "upload");
+  CK(up(h->adj_edge, hm.adj_edge.data(), (size_t)hm.nnz * 4), "upload");
+  CK(up(h->edges, hm.edges.data(), (size_t)hm.nE * 8), "upload");
+  CK(up(h->edge_w, hm.edge_w.data(), (size_t)hm.nE * 4), "upload");
+  CK(up(h->lumped, hm.lumped.data(), nV * 4), "upload");
+  CK(up(h->Mdiag, hm.Mdiag.data(), nV * 4), "upload");
+  CK(up(h->Moff, hm.Moff.data(), (size_t)hm.nnz * 4), "upload");
+  CK(up(h->Adiag, hm.Adiag.data(), nV * 4), "upload");
+  CK(up(h->Aoff, hm.Aoff.data(), (size_t)hm.nnz * 4), "upload");
+  CK(up(h->dinv, hm.dinv.data(), nV * 4), "upload");
+  st = device_setup(h, s, true);
+  if (st) return st;
+  guard.keep = true;
+  *out = h;
+  return MREG_OK;
+}
+
+mreg_status mreg_reset(mreg_handle* h, void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  return device_setup(h, (cudaStream_t)stream, false);
+}
+
+mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  if (n_iters < 0) return fail(MREG_ERR_INVALID_ARG, "n_iters must be >= 0");
+  if (n_iters == 0) return MREG_OK;
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  // Long runs are split into launches of at most kChunk iterations, which
+  // bounds the barrier counter of one launch.
+  for (int it0 = 0; it0 < n_iters; it0 += kChunk) {
+    const int n = std::min(kChunk, n_iters - it0);
+    const mreg::IterArgs a = h->iter_args(n, it0);
+    CK(mreg::launch_iterate(h->form, h->grad, a, h->grid, h->block, (cudaStream_t)stream),
+       "iteration kernel launch");
+    h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
+  }
+  h->iterations_done += n_iters;
+  h->last_n_iters = n_iters;
+  return MREG_OK;
+}
+
+mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  mreg::WarpArgs a{};
+  a.W = h->W;
+  a.H = h->H;
+  a.nT = h->nT;
+  a.V = h->V;
+  a.tri = h->tri;
+  a.pix_tri = h->pix_tri;
+  a.u = h->u;
+  a.cTe = h->cTe;
+  a.Re = h->Re;
+  a.out = out_dev;
+  a.part = h->warp_part;
+  CK(mreg::launch_warp_msd(a, h->warp_grid, 1.0 / ((double)h->W * h->H), msd_dev,
+                           (cudaStream_t)stream),
+     "warp kernel launch");
+  return MREG_OK;
+}
+
+mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream) {
+  if (!h || !out_host) return fail(MREG_ERR_INVALID_ARG, "handle or output is NULL");
+  mreg_status st = mreg_warp(h, nullptr, h->msd, stream);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(out_host, h->msd, sizeof(double), cudaMemcpyDeviceToHost, s), "copy MSD");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  return MREG_OK;
+}
+
+mreg_status mreg_energy(mreg_handle* h, double* out_host, void* stream) {
+  if (!h || !out_host) return fail(MREG_ERR_INVALID_ARG, "handle or output is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(out_host, h->last, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  return MREG_OK;
+}
+
+mreg_status mreg_get_u(mreg_handle* h, float* dst, int32_t dst_on_device, void* stream) {
+  if (!h || !dst) return fail(MREG_ERR_INVALID_ARG, "handle or destination is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(dst, h->u, sizeof(float2) * h->nV,
+                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+     "copy u");
+  if (!dst_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+  return MREG_OK;
+}
+
+mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, void* stream) {
+  if (!h || !src) return fail(MREG_ERR_INVALID_ARG, "handle or source is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  if (!src_on_device)
+    for (int i = 0; i < 2 * h->nV; ++i)
+      if (!std::isfinite(src[i])) return fail(MREG_ERR_NONFINITE, "u[%d] is not finite", i / 2);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->u, src, sizeof(float2) * h->nV,
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+     "copy u");
+  if (!src_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+  return MREG_OK;
+}
+
+mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst_on_device,
+                           int64_t* count_out, void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  const void* src = nullptr;
+  int64_t count = 0;
+  size_t esize = 4;
+  const int64_t npx = (int64_t)h->W * h->H;
+  const int hist = std::min(h->last_n_iters, kHistCap);
+  switch (field) {
+    case MREG_FIELD_U: src = h->u, count = 2 * (int64_t)h->nV; break;
+    case MREG_FIELD_FORCE: src = h->F + (size_t)h->last_force_buf * h->nV, count = 2 * (int64_t)h->nV; break;
+    case MREG_FIELD_TE_NODES: src = h->f, count = h->nV; break;
+    case MREG_FIELD_RE_NODES: src = h->ReV, count = h->nV; break;
+    case MREG_FIELD_COEF_RE: src = h->cRe, count = npx; break;
+    case MREG_FIELD_COEF_TE: src = h->cTe, count = npx; break;
+    case MREG_FIELD_PIXEL_TRI: src = h->pix_tri, count = npx; break;
+    case MREG_FIELD_ENERGY: src = h->energy_hist, count = hist, esize = 8; break;
+    case MREG_FIELD_PCG_ITERS: src = h->pcg_it_hist, count = hist; break;
+    case MREG_FIELD_PCG_RESID: src = h->pcg_res_hist, count = hist, esize = 8; break;
+    default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
+  }
+  if (count_out) *count_out = count;
+  if (!dst || count == 0) return MREG_OK;
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(dst, src, (size_t)count * esize,
+                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+     "copy field");
+  if (!dst_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+  return MREG_OK;
+}
+
+mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  double last[8];
+  int status = 0;
+  CK(cudaMemcpyAsync(last, h->last, sizeof last, cudaMemcpyDeviceToHost, s), "copy stats");
+  CK(cudaMemcpyAsync(&status, h->status, sizeof status, cudaMemcpyDeviceToHost, s), "copy status");
+  CK(cudaStreamSynchronize(s), "synchronize");
+  if (out) {
+    std::memset(out, 0, sizeof *out);
+    out->iterations_done = h->iterations_done;
+    out->last_energy = last[0];
+    out->last_rel_resid = last[1];
+    out->last_pcg_iters = (int32_t)last[2];
+    out->max_pcg_iters = (int32_t)last[3];
+    out->not_converged = (int32_t)last[4];
+    out->grid_blocks = h->grid;
+    out->block_size = h->block;
+    out->device_status = status;
+  }
+  if (status & mreg::kStatusBarrierTimeout)
+    return fail(MREG_ERR_DEVICE_CHECK, "a grid barrier of the iteration kernel timed out");
+  if (status & mreg::kStatusNotConverged)
+    return fail(MREG_ERR_NOT_CONVERGED, "%d solves stopped at the CG iteration cap (%d)",
+                (int)last[4], h->opts.pcg_maxit);
+  return MREG_OK;
+}
+
+void mreg_destroy(mreg_handle* h) {
+  if (!h) return;
+  if (h->arena) {
+    cudaSetDevice(h->dev);
+    cudaFree(h->arena);
+  }
+  delete h;
+}
+
+const char* mreg_last_error(void) { return g_last_error.c_str(); }
+
+int32_t mreg_version(void) { return MREG_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal declarations of the registration library: device-side argument
+// blocks and the kernel launchers (one per hot-path step).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mreg {
+
+// Device status bits (also read by the host).
+constexpr int kStatusNotConverged = 1;   // a CG solve stopped at its cap
+constexpr int kStatusBarrierTimeout = 2; // a grid barrier wait gave up
+constexpr int kStatusAbort = 4;          // every block must leave the kernel
+
+// Floats in one block's reduction record (partial sums carried through one
+// grid barrier), and the largest number of warps per block.
+constexpr int kRec = 12;
+constexpr int kMaxWarps = 32;
+
+// Update / solve forms of the iteration kernel.
+enum Form : int {
+  kFormExplicit = 0,     // S0: Eq. 5 + Eq. 14
+  kFormUmbrella = 1,     // S1: ((1+l) D_m - l W) u' = D_m (u - tau F)
+  kFormFemNodes = 2,     // S2, nodal (lumped) quadrature
+  kFormFemEdges = 3      // S2, edge-midpoint quadrature (needs the spline gradient)
+};
+
+// Everything the persistent iteration kernel reads or writes.
+struct IterArgs {
+  int nV, nE, W, H, n_iters, it0, maxit, hist_cap;   // it0: history index of iteration 0
+  float tau, lam, area_floor, rtol2;
+  float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
+  // read-only mesh / operator data
+  const float2* V;
+  const int* inc_ptr;    // nV + 1, incident triangles (ascending triangle index)
+  const int2* inc_opp;   // per incidence: the triangle's other two corners,
+                         // counter-clockwise after the node
+  const int* adj_ptr;    // nV + 1, off-diagonal node graph (ascending)
+  const int* adj_col;
+  const int* adj_edge;   // edge id of every adjacency entry (edge form)
+  const int2* edges;     // nE unique edges (a < b)
+  const float* edge_w;   // quadrature weight of each edge midpoint
+  const float* Mdiag;    // FEM: mass matrix diagonal / off-diagonal
+  const float* Moff;
+  const float* Adiag;    // FEM: M + l K
+  const float* Aoff;
+  const float* dinv;     // 1 / diag(A), Jacobi preconditioner (S1, S2)
+  const float* lumped;   // FEM nodal quadrature weight A(V_a)/3
+  const float* cTe;      // B-spline coefficients of Te, dense W x H
+  const float* ReV;      // Re at the undeformed nodes
+  const float* ReQ;      // Re at the undeformed edge midpoints
+  // mutable state
+  float2* u;             // displacement; also the CG iterate
+  float* f;              // Te(V+u)
+  float2* F;             // force, two buffers of nV (iteration parity)
+  float2* u0;            // S0: u - tau F, two buffers of nV (iteration parity)
+  float2* hq;            // edge form: per-edge force contribution
+  float2* r;             // CG residual (FP32)
+  float2* z;             // preconditioned residual
+  float2* p0;            // CG directions (ping-pong)
+  float2* p1;
+  float2* q;             // A p
+  float2* rt;            // true residual (FP32 copy) for restarts
+  float4* b;             // right-hand side, float-float {x.hi, x.lo, y.hi, y.lo}
+  // reductions / control
+  float* part;           // 2 * grid * kRec partial sums (two halves, alternating)
+  unsigned long long* bar;  // barrier counter (zeroed before each launch)
+  int* status;           // device status bits
+  double* energy_hist;   // per-iteration data energy (hist_cap entries)
+  int* pcg_it_hist;
+  double* pcg_res_hist;
+  double* last;          // [0] last energy, [1] last rel. residual, [2] last CG its,
+                         // [3] max CG its, [4] not-converged count
+};
+
+struct WarpArgs {
+  int W, H, nT;
+  const float2* V;
+  const int* tri;
+  const int* pix_tri;
+  const float2* u;
+  const float* cTe;
+  const float* Re;       // dense W x H reference pixels
+  float* out;            // optional registered image
+  float* part;           // one reduction record (kRec floats) per block
+};
+
+// Launchers (return the first CUDA error, cudaSuccess otherwise).
+cudaError_t launch_prefilter(const float* img, int64_t stride, float* tmp, float* coef, int W,
+                             int H, cudaStream_t s);
+cudaError_t launch_sample_nodes(const float* coef, int W, int H, const float2* V, int n,
+                                float* out, cudaStream_t s);
+cudaError_t launch_sample_edges(const float* coef, int W, int H, const float2* V,
+                                const int2* edges, int nE, float* out, cudaStream_t s);
+cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int H, int* pix_tri,
+                             int* uncovered, cudaStream_t s);
+cudaError_t launch_count_nonfinite(const float* img, int W, int H, int64_t stride, int* count,
+                                   cudaStream_t s);
+cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
+                            cudaStream_t s);
+int warp_grid_blocks(int W, int H, int num_sms);
+
+// Iteration kernel: occupancy query and cooperative launch.
+cudaError_t iterate_max_blocks(int form, int grad, int block, int* max_blocks_per_sm);
+cudaError_t launch_iterate(int form, int grad, const IterArgs& a, int grid, int block,
+                           cudaStream_t s);
+
+}  // namespace mreg

@@ -1,0 +1,312 @@
+"""Thin Python binding of the C ABI in ``include/mreg.h`` (ctypes).
+
+Only argument marshalling lives here: every step of the registration runs in
+the CUDA library ``lib/libmreg.so``.  There is no CPU fallback: if the
+library is missing or fails to load, :func:`load` raises.
+
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (torch is
+used for device memory and streams only).  ``stream`` arguments accept a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or ``None`` (torch's
+current stream when torch is imported and CUDA is initialised, else the
+legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmreg.so")
+
+# mreg_status
+MREG_OK = 0
+MREG_ERR_INVALID_ARG = 1
+MREG_ERR_BAD_MESH = 2
+MREG_ERR_SIZE_MISMATCH = 3
+MREG_ERR_NONFINITE = 4
+MREG_ERR_CUDA = 5
+MREG_ERR_OOM = 6
+MREG_ERR_NOT_CONVERGED = 7
+MREG_ERR_DEVICE_CHECK = 8
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MESH", 3: "SIZE_MISMATCH", 4: "NONFINITE",
+                5: "CUDA", 6: "OOM", 7: "NOT_CONVERGED", 8: "DEVICE_CHECK"}
+
+MREG_MODE_EXPLICIT = 0
+MREG_MODE_UMBRELLA_IMPLICIT = 1
+MREG_MODE_FEM_IMPLICIT = 2
+MREG_GRAD_MESH = 0
+MREG_GRAD_SPLINE = 1
+MREG_QUAD_NODES = 0
+MREG_QUAD_EDGE_MIDPOINTS = 1
+
+MREG_FIELD_U = 0
+MREG_FIELD_FORCE = 1
+MREG_FIELD_TE_NODES = 2
+MREG_FIELD_RE_NODES = 3
+MREG_FIELD_COEF_RE = 4
+MREG_FIELD_COEF_TE = 5
+MREG_FIELD_PIXEL_TRI = 6
+MREG_FIELD_ENERGY = 7
+MREG_FIELD_PCG_ITERS = 8
+MREG_FIELD_PCG_RESID = 9
+
+MODES = {"S0": MREG_MODE_EXPLICIT, "S1": MREG_MODE_UMBRELLA_IMPLICIT, "S2": MREG_MODE_FEM_IMPLICIT}
+GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
+QUADS = {"Q0": MREG_QUAD_NODES, "Q1": MREG_QUAD_EDGE_MIDPOINTS}
+
+
+class mreg_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_tris", C.c_int32),
+                ("xy", C.POINTER(C.c_float)), ("tri", C.POINTER(C.c_int32))]
+
+
+class mreg_image(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("row_stride", C.c_int64),
+                ("data", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class mreg_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
+                ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
+                ("block_size", C.c_int32), ("grid_blocks", C.c_int32)]
+
+
+class mreg_stats_t(C.Structure):
+    _fields_ = [("iterations_done", C.c_int32), ("last_pcg_iters", C.c_int32),
+                ("max_pcg_iters", C.c_int32), ("not_converged", C.c_int32),
+                ("last_rel_resid", C.c_double), ("last_energy", C.c_double),
+                ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
+                ("device_status", C.c_int32)]
+
+
+EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
+           "mreg_msd", "mreg_energy", "mreg_get_u", "mreg_set_u", "mreg_get_field",
+           "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version"]
+
+_lib = None
+
+
+class MregError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load the CUDA library (once).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1411_2141_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "mreg_default_options": ([C.POINTER(mreg_options)], i32),
+        "mreg_create": ([C.POINTER(mreg_mesh), C.POINTER(mreg_image), C.POINTER(mreg_image),
+                         dbl, dbl, C.POINTER(mreg_options), vp, C.POINTER(vp)], i32),
+        "mreg_reset": ([vp, vp], i32),
+        "mreg_step": ([vp, i32, vp], i32),
+        "mreg_warp": ([vp, vp, vp, vp], i32),
+        "mreg_msd": ([vp, C.POINTER(dbl), vp], i32),
+        "mreg_energy": ([vp, C.POINTER(dbl), vp], i32),
+        "mreg_get_u": ([vp, vp, i32, vp], i32),
+        "mreg_set_u": ([vp, vp, i32, vp], i32),
+        "mreg_get_field": ([vp, i32, vp, i32, C.POINTER(i64), vp], i32),
+        "mreg_stats": ([vp, C.POINTER(mreg_stats_t), vp], i32),
+        "mreg_destroy": ([vp], None),
+        "mreg_last_error": ([], C.c_char_p),
+        "mreg_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != MREG_OK:
+        raise MregError(st, where, load().mreg_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream or None
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def default_options() -> mreg_options:
+    o = mreg_options()
+    _check(load().mreg_default_options(C.byref(o)), "mreg_default_options")
+    return o
+
+
+def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
+                 block_size=0, grid_blocks=0) -> mreg_options:
+    o = default_options()
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
+    o.quad = QUADS[quad] if isinstance(quad, str) else int(quad)
+    if lam is not None:
+        o.lambda_ = float(lam)
+    if pcg_rtol is not None:
+        o.pcg_rtol = float(pcg_rtol)
+    if pcg_maxit is not None:
+        o.pcg_maxit = int(pcg_maxit)
+    o.block_size = int(block_size)
+    o.grid_blocks = int(grid_blocks)
+    return o
+
+
+def _image(img, keep: list) -> mreg_image:
+    im = mreg_image()
+    if _is_torch_cuda(img):
+        if str(img.dtype) != "torch.float32" or img.dim() != 2 or img.stride(1) != 1:
+            raise ValueError("device images must be 2-D float32 tensors with unit column stride")
+        im.height, im.width = int(img.shape[0]), int(img.shape[1])
+        im.row_stride = int(img.stride(0))
+        im.data = img.data_ptr()
+        im.on_device = 1
+        keep.append(img)
+    else:
+        a = np.ascontiguousarray(img, dtype=np.float32)
+        if a.ndim != 2:
+            raise ValueError("images must be 2-D")
+        im.height, im.width = a.shape
+        im.row_stride = a.shape[1]
+        im.data = a.ctypes.data
+        im.on_device = 0
+        keep.append(a)
+    return im
+
+
+class Registration:
+    """One registration problem on the current CUDA device (wraps a handle)."""
+
+    def __init__(self, V, T, Re, Te, alpha: float, tau: float, options: mreg_options | None = None,
+                 stream=None, **kw):
+        lib = load()
+        if options is None:
+            options = make_options(**kw)
+        keep: list = []
+        Vh = np.ascontiguousarray(V, dtype=np.float32)
+        Th = np.ascontiguousarray(T, dtype=np.int32)
+        if Vh.ndim != 2 or Vh.shape[1] != 2 or Th.ndim != 2 or Th.shape[1] != 3:
+            raise ValueError("V must be (n, 2) and T (m, 3)")
+        mesh = mreg_mesh(Vh.shape[0], Th.shape[0], Vh.ctypes.data_as(C.POINTER(C.c_float)),
+                         Th.ctypes.data_as(C.POINTER(C.c_int32)))
+        re = _image(Re, keep)
+        te = _image(Te, keep)
+        h = C.c_void_p()
+        self._h = None
+        _check(lib.mreg_create(C.byref(mesh), C.byref(re), C.byref(te), float(alpha), float(tau),
+                               C.byref(options), _stream_ptr(stream), C.byref(h)), "mreg_create")
+        self._h = h
+        self.n_nodes = int(Vh.shape[0])
+        self.n_tris = int(Th.shape[0])
+        self.height, self.width = int(re.height), int(re.width)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.mreg_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def reset(self, stream=None):
+        _check(load().mreg_reset(self._h, _stream_ptr(stream)), "mreg_reset")
+
+    def step(self, n_iters: int, stream=None):
+        _check(load().mreg_step(self._h, int(n_iters), _stream_ptr(stream)), "mreg_step")
+
+    def warp(self, out=None, msd_out=None, stream=None):
+        """Asynchronous warp into device tensors ``out`` (H x W float32) and
+        ``msd_out`` (1 float64), either may be None."""
+        po = out.data_ptr() if out is not None else None
+        pm = msd_out.data_ptr() if msd_out is not None else None
+        _check(load().mreg_warp(self._h, po, pm, _stream_ptr(stream)), "mreg_warp")
+
+    def msd(self, stream=None) -> float:
+        v = C.c_double()
+        _check(load().mreg_msd(self._h, C.byref(v), _stream_ptr(stream)), "mreg_msd")
+        return v.value
+
+    def energy(self, stream=None) -> float:
+        v = C.c_double()
+        _check(load().mreg_energy(self._h, C.byref(v), _stream_ptr(stream)), "mreg_energy")
+        return v.value
+
+    def get_u(self, out=None, stream=None) -> np.ndarray:
+        if out is not None and _is_torch_cuda(out):
+            _check(load().mreg_get_u(self._h, out.data_ptr(), 1, _stream_ptr(stream)), "mreg_get_u")
+            return out
+        u = np.empty((self.n_nodes, 2), np.float32)
+        _check(load().mreg_get_u(self._h, u.ctypes.data, 0, _stream_ptr(stream)), "mreg_get_u")
+        return u
+
+    def set_u(self, u, stream=None):
+        if _is_torch_cuda(u):
+            _check(load().mreg_set_u(self._h, u.data_ptr(), 1, _stream_ptr(stream)), "mreg_set_u")
+            return
+        a = np.ascontiguousarray(u, dtype=np.float32)
+        if a.shape != (self.n_nodes, 2):
+            raise ValueError("u must be (n_nodes, 2)")
+        _check(load().mreg_set_u(self._h, a.ctypes.data, 0, _stream_ptr(stream)), "mreg_set_u")
+
+    def get_field(self, field: int, stream=None) -> np.ndarray:
+        lib = load()
+        n = C.c_int64()
+        _check(lib.mreg_get_field(self._h, field, None, 0, C.byref(n), _stream_ptr(stream)),
+               "mreg_get_field")
+        dtype = {MREG_FIELD_PIXEL_TRI: np.int32, MREG_FIELD_PCG_ITERS: np.int32,
+                 MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64}.get(field, np.float32)
+        out = np.empty(n.value, dtype)
+        if n.value:
+            _check(lib.mreg_get_field(self._h, field, out.ctypes.data, 0, None, _stream_ptr(stream)),
+                   "mreg_get_field")
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
+            out = out.reshape(-1, 2)
+        elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI):
+            out = out.reshape(self.height, self.width)
+        return out
+
+    def stats(self, stream=None, check: bool = True) -> dict:
+        s = mreg_stats_t()
+        st = load().mreg_stats(self._h, C.byref(s), _stream_ptr(stream))
+        if check:
+            _check(st, "mreg_stats")
+        d = {k: getattr(s, k) for k, _ in mreg_stats_t._fields_}
+        d["status"] = st
+        return d

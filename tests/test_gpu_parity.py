@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances
+  * end to end (the accuracy target of the FP32 form): node displacements
+    within 1e-4 px and MSD within 1e-5 relative of the oracle;
+  * per step, from FP32 arithmetic: the prefilter is a stable recursion whose
+    2-D gain is at most 9 (3 per pass), so coefficients agree to a few FP32
+    ulps of the largest value (tolerance 5e-6 relative to max |c|); a spline
+    sample sums 16 taps with weights summing to 1 (5e-6 of max |c|); the
+    pixel -> triangle map is index work, compared bit for bit;
+  * force: the mesh gradient divides value differences of neighbouring
+    samples by edge lengths of a few px, so its absolute error is a few
+    sample ulps per px (tolerance 2e-5 relative to max |F|).
+"""
+import numpy as np
+import pytest
+
+from oracle import bspline, register
+from paper_1411_2141_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U_TOL = 1e-4       # px
+MSD_RTOL = 1e-5
+MODES = [("S0", "G0", "Q0"), ("S0", "G1", "Q0"), ("S1", "G0", "Q0"), ("S1", "G1", "Q0"),
+         ("S2", "G0", "Q0"), ("S2", "G1", "Q0"), ("S2", "G1", "Q1")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_2141_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def mreg():
+    from paper_1411_2141_gb300 import mreg as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def c0():
+    return inputs.make_case(inputs.config_spec(0))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return inputs.make_case(inputs.config_spec(1))
+
+
+def _reg(mreg, case, mode="S0", grad="G0", quad="Q0", **kw):
+    return mreg.Registration(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
+                             mode=mode, grad=grad, quad=quad, **kw)
+
+
+def _oracle(case, mode="S0", grad="G0", quad="Q0"):
+    return register.Problem(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
+                            mode, grad, quad)
+
+
+def _ragged_case(H, W, seed):
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    Re = (np.sin(xs / 3.1 + 0.3) * np.cos(ys / 4.3) + 0.1 * rng.normal(size=(H, W))).astype(np.float32)
+    Te = (np.sin((xs + 0.7) / 3.1 + 0.3) * np.cos((ys - 0.4) / 4.3)
+          + 0.1 * rng.normal(size=(H, W))).astype(np.float32)
+    n = max(4, min(300, (H * W) // 12))
+    V, T = inputs.make_mesh(Te, n, seed)
+    spec = inputs.CaseSpec(side=max(H, W), n_nodes=len(V), seed=seed)
+    return inputs.Case(spec=spec, Re=Re, Te=Te, V=V, T=T, d=np.zeros((H, W, 2)))
+
+
+RAGGED = [(2, 2), (3, 7), (37, 53), (5, 200), (200, 5), (64, 65), (24, 25), (130, 70), (300, 17)]
+
+
+@pytest.mark.parametrize("hw", RAGGED)
+def test_prefilter_and_node_samples(mreg, hw):
+    case = _ragged_case(*hw, seed=hw[0] * 1000 + hw[1])
+    with _reg(mreg, case) as r:
+        for field, img in ((mreg.MREG_FIELD_COEF_RE, case.Re), (mreg.MREG_FIELD_COEF_TE, case.Te)):
+            got = r.get_field(field)
+            ref = bspline.prefilter_2d(img)
+            tol = 5e-6 * np.abs(ref).max()
+            err = np.abs(got - ref).max()
+            assert err <= tol, (hw, field, err, tol)
+        pb = _oracle(case)
+        got = r.get_field(mreg.MREG_FIELD_RE_NODES)
+        tol = 5e-6 * np.abs(pb.cRe).max()
+        assert np.abs(got - pb.ReV).max() <= tol
+
+
+def test_prefilter_config0(mreg, c0):
+    with _reg(mreg, c0) as r:
+        got = r.get_field(mreg.MREG_FIELD_COEF_TE)
+    ref = bspline.prefilter_2d(c0.Te)
+    assert np.abs(got - ref).max() <= 5e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("which", ["c0", (37, 53), (130, 70), (2, 2)])
+def test_pixel_map_bit_exact(mreg, c0, which):
+    case = c0 if which == "c0" else _ragged_case(*which, seed=7)
+    with _reg(mreg, case) as r:
+        got = r.get_field(mreg.MREG_FIELD_PIXEL_TRI)
+    H, W = case.Re.shape
+    ref = register.locate_pixels(case.V, case.T, W, H)
+    assert (ref >= 0).all()
+    assert np.array_equal(got, ref.astype(np.int32))
+
+
+@pytest.mark.parametrize("mode,grad,quad", MODES)
+def test_first_iteration_fields(mreg, c0, mode, grad, quad):
+    pb = _oracle(c0, mode, grad, quad)
+    u0 = np.zeros((pb.n, 2))
+    f, rr, g = pb.sample(u0)
+    F = pb.force(u0, f, rr, g)
+    u1 = pb.update(u0, F)
+    f1, _, _ = pb.sample(u1)   # TE_NODES describes the current u after the step
+    with _reg(mreg, c0, mode, grad, quad) as r:
+        r.step(1)
+        got_f = r.get_field(mreg.MREG_FIELD_TE_NODES)
+        got_F = r.get_field(mreg.MREG_FIELD_FORCE)
+        got_u = r.get_u()
+        e = r.get_field(mreg.MREG_FIELD_ENERGY)
+        r.stats()
+    if quad != "Q1":
+        assert np.abs(got_f - f1).max() <= 5e-6 * np.abs(pb.cTe).max()
+    assert np.abs(got_F - F).max() <= 2e-5 * np.abs(F).max()
+    assert np.abs(got_u - u1).max() <= 1e-6
+    assert abs(e[0] - pb.data_energy(u0)) <= 1e-5 * pb.data_energy(u0)
+
+
+@pytest.mark.parametrize("mode,grad,quad", MODES)
+def test_registration_config0(mreg, c0, mode, grad, quad):
+    n = c0.spec.n_iter
+    pb = _oracle(c0, mode, grad, quad)
+    u_ref, e_ref = pb.run(n)
+    with _reg(mreg, c0, mode, grad, quad) as r:
+        r.step(n)
+        u = r.get_u()
+        msd = r.msd()
+        e = r.get_field(mreg.MREG_FIELD_ENERGY)
+        st = r.stats()
+        if mode != "S0":
+            its = r.get_field(mreg.MREG_FIELD_PCG_ITERS)
+            res = r.get_field(mreg.MREG_FIELD_PCG_RESID)
+            assert (its > 0).all() and (res <= 1e-7).all()
+    msd_ref = pb.msd(u_ref)
+    du = np.abs(u - u_ref).max()
+    dm = abs(msd - msd_ref) / msd_ref
+    print(f"{mode}{grad}{quad}: du={du:.2e} dmsd={dm:.2e} its={st['max_pcg_iters']}")
+    assert du <= U_TOL
+    assert dm <= MSD_RTOL
+    np.testing.assert_allclose(e, e_ref, rtol=1e-5)
+
+
+@pytest.mark.parametrize("mode", ["S1", "S0"])
+def test_registration_config1_full_size(mreg, c1, mode):
+    """The 512^2 / 20k-node workload in the launch configuration the bench
+    times (automatic grid), full 200 iterations."""
+    n = c1.spec.n_iter
+    pb = _oracle(c1, mode)
+    u_ref, _ = pb.run(n)
+    with _reg(mreg, c1, mode) as r:
+        r.step(n)
+        u = r.get_u()
+        msd = r.msd()
+        r.stats()
+    msd_ref = pb.msd(u_ref)
+    du = np.abs(u - u_ref).max()
+    dm = abs(msd - msd_ref) / msd_ref
+    print(f"c1 {mode}: du={du:.2e} dmsd={dm:.2e}")
+    assert du <= U_TOL
+    assert dm <= MSD_RTOL
+
+
+def test_warp_image(mreg, c0):
+    pb = _oracle(c0, "S1")
+    u_ref, _ = pb.run(20)
+    R_ref = pb.warp(u_ref)
+    with _reg(mreg, c0, "S1") as r:
+        r.step(20)
+        out = torch.empty(c0.Re.shape, dtype=torch.float32, device="cuda")
+        msd_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+        r.warp(out, msd_dev)
+        torch.cuda.synchronize()
+        R = out.cpu().numpy()
+        msd = float(msd_dev.cpu()[0])
+    assert np.abs(R - R_ref).max() <= 1e-5
+    assert abs(msd - pb.msd(u_ref)) <= MSD_RTOL * pb.msd(u_ref)
+
+
+def test_msd_at_zero_displacement_is_pixel_mean(mreg, c0):
+    with _reg(mreg, c0) as r:
+        m = r.msd()
+    ref = float(np.mean((c0.Te.astype(np.float64) - c0.Re) ** 2))
+    assert abs(m - ref) <= 1e-6 * ref
+
+
+def test_runs_are_bitwise_repeatable(mreg, c0):
+    outs = []
+    for _ in range(2):
+        with _reg(mreg, c0, "S1") as r:
+            r.step(30)
+            outs.append((r.get_u(), r.msd()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+def test_checkpoint_resume_is_bitwise(mreg, c0):
+    with _reg(mreg, c0, "S1") as r:
+        r.step(20)
+        u20 = r.get_u()
+    with _reg(mreg, c0, "S1") as r:
+        r.step(10)
+        u10 = r.get_u()
+    with _reg(mreg, c0, "S1") as r:
+        r.set_u(u10)
+        r.step(10)
+        assert np.array_equal(r.get_u(), u20)
+
+
+def test_reset_restarts_the_registration(mreg, c0):
+    with _reg(mreg, c0, "S0") as r:
+        r.step(15)
+        a = r.get_u()
+        r.reset()
+        assert np.abs(r.get_u()).max() == 0.0
+        r.step(15)
+        assert np.array_equal(r.get_u(), a)
+
+
+def test_launch_shape_changes_only_rounding(mreg, c0):
+    res = []
+    for grid in (0, 3, 17):
+        with _reg(mreg, c0, "S1", grid_blocks=grid, block_size=128) as r:
+            r.step(30)
+            res.append(r.get_u())
+    for u in res[1:]:
+        assert np.abs(u - res[0]).max() <= 1e-5
+
+
+def test_device_images_with_row_stride(mreg, c0):
+    H, W = c0.Re.shape
+    big_re = torch.zeros((H, W + 13), dtype=torch.float32, device="cuda")
+    big_te = torch.zeros((H, W + 13), dtype=torch.float32, device="cuda")
+    big_re[:, :W] = torch.from_numpy(c0.Re)
+    big_te[:, :W] = torch.from_numpy(c0.Te)
+    with mreg.Registration(c0.V, c0.T, big_re[:, :W], big_te[:, :W], 0.1, 1.0, mode="S1") as r:
+        r.step(10)
+        ud = r.get_u()
+    with _reg(mreg, c0, "S1") as r:
+        r.step(10)
+        uh = r.get_u()
+    assert np.array_equal(ud, uh)
+
+
+def test_nonfinite_device_image_is_rejected(mreg, c0):
+    re = torch.from_numpy(c0.Re).cuda()
+    te = torch.from_numpy(c0.Te).cuda()
+    te[5, 7] = float("nan")
+    with pytest.raises(mreg.MregError) as e:
+        mreg.Registration(c0.V, c0.T, re, te, 0.1, 1.0)
+    assert e.value.status == mreg.MREG_ERR_NONFINITE
+
+
+def test_zero_iterations_and_tiny_image(mreg):
+    case = _ragged_case(2, 2, seed=1)
+    for mode in ("S0", "S1", "S2"):
+        pb = _oracle(case, mode)
+        u_ref, _ = pb.run(3)
+        with _reg(mreg, case, mode) as r:
+            r.step(0)
+            assert np.abs(r.get_u()).max() == 0.0
+            r.step(3)
+            assert np.abs(r.get_u() - u_ref).max() <= 1e-6
+            assert abs(r.msd() - pb.msd(u_ref)) <= 1e-5 * max(pb.msd(u_ref), 1e-12)
+
+
+def test_pcg_cap_is_reported(mreg, c0):
+    with _reg(mreg, c0, "S1", pcg_maxit=1, pcg_rtol=1e-12) as r:
+        r.step(3)
+        st = r.stats(check=False)
+    assert st["status"] == mreg.MREG_ERR_NOT_CONVERGED
+    assert st["not_converged"] == 3 and st["max_pcg_iters"] == 1
