@@ -226,6 +226,34 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream);
  * NULL is accepted.                                                         */
 void mreg_destroy(mreg_handle* h);
 
+/* Largest image (width * height) that mreg_prefilter_noalloc accepts. */
+#define MREG_NOALLOC_MAX_PIXELS (1024 * 1024)
+
+/* B-spline coefficients of one image without allocating device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, such as code running while a stream is captured
+ * into a CUDA graph, hosts whose memory pool owns all device memory, and
+ * loops that must not pay for a device-synchronising allocation.  It runs
+ * the same prefilter as mreg_create (step a0) on a caller's image and writes
+ * the coefficients to the caller's buffer; its only scratch is a fixed
+ * 4 MiB array inside the library (MREG_NOALLOC_MAX_PIXELS floats), which
+ * every GPU that loads the library holds until the process exits.
+ *   img_dev    device image, width x height float32, row stride row_stride
+ *              (elements, >= width)
+ *   coef_dev   device output, width x height float32, row stride width;
+ *              must not overlap img_dev
+ *   stream     cudaStream_t as void*; the call is asynchronous
+ * Errors: INVALID_ARG for NULL pointers, images smaller than 2x2, a row
+ * stride below the width, or width * height > MREG_NOALLOC_MAX_PIXELS; CUDA
+ * if a launch fails.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) for that device, so make that first
+ * call before any stream capture.  All calls share the one scratch array:
+ * calls that may overlap on the GPU (different streams, or several host
+ * threads) race on it and must be serialised by the caller.              */
+mreg_status mreg_prefilter_noalloc(const float* img_dev, int64_t row_stride, float* coef_dev,
+                                   int32_t width, int32_t height, void* stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char* mreg_last_error(void);
 

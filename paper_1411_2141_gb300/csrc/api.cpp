@@ -235,6 +235,12 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace mreg {
+// Record an error message for mreg_last_error() (used by the entry points
+// defined in other translation units).
+mreg_status set_error(mreg_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace mreg
+
 struct mreg_handle {
   int dev = 0, num_sms = 0;
   int W = 0, H = 0, nV = 0, nT = 0, nE = 0, nnz = 0;

@@ -83,7 +83,10 @@ class mreg_stats_t(C.Structure):
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
            "mreg_msd", "mreg_energy", "mreg_get_u", "mreg_set_u", "mreg_get_field",
-           "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version"]
+           "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
+           "mreg_prefilter_noalloc"]
+
+NOALLOC_MAX_PIXELS = 1024 * 1024
 
 _lib = None
 
@@ -121,6 +124,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_destroy": ([vp], None),
         "mreg_last_error": ([], C.c_char_p),
         "mreg_version": ([], i32),
+        "mreg_prefilter_noalloc": ([vp, i64, vp, i32, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -151,6 +155,20 @@ def _stream_ptr(stream) -> int | None:
 
 def _is_torch_cuda(x) -> bool:
     return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def prefilter_noalloc(img, out, stream=None):
+    """B-spline coefficients of a device image (2-D float32 torch tensor with
+    unit column stride) into ``out`` (contiguous, same shape) without any
+    device allocation; asynchronous on ``stream``."""
+    if str(img.dtype) != "torch.float32" or img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("img must be a 2-D float32 tensor with unit column stride")
+    if tuple(out.shape) != tuple(img.shape) or not out.is_contiguous():
+        raise ValueError("out must be contiguous with the image's shape")
+    H, W = int(img.shape[0]), int(img.shape[1])
+    _check(load().mreg_prefilter_noalloc(img.data_ptr(), int(img.stride(0)), out.data_ptr(), W, H,
+                                         _stream_ptr(stream)), "mreg_prefilter_noalloc")
+    return out
 
 
 def default_options() -> mreg_options:
