@@ -263,7 +263,8 @@ struct mreg_handle {
         *Aoff = nullptr, *dinv = nullptr;
   float *ReV = nullptr, *ReQ = nullptr, *f = nullptr;
   float2 *u = nullptr, *F = nullptr, *u0 = nullptr, *hq = nullptr;
-  float2 *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *rt = nullptr;
+  float4* cg = nullptr;
+  float2* rt = nullptr;
   float4* b = nullptr;
   float* part = nullptr;
   unsigned long long* bar = nullptr;
@@ -314,11 +315,7 @@ struct mreg_handle {
     a.F = F;
     a.u0 = u0;
     a.hq = hq;
-    a.r = r;
-    a.z = z;
-    a.p0 = p0;
-    a.p1 = p1;
-    a.q = q;
+    a.cg = cg;
     a.rt = rt;
     a.b = b;
     a.part = part;
@@ -532,8 +529,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_Ad = take(nV * 4), o_Ao = take(nnz * 4), o_dinv = take(nV * 4),
                o_ReV = take(nV * 4), o_ReQ = take(nE * 4), o_f = take(nV * 4), o_u = take(nV * 8),
                o_F = take(2 * nV * 8), o_u0 = take(2 * nV * 8), o_hq = take(nE * 8),
-               o_r = take(nV * 8), o_z = take(nV * 8), o_p0 = take(nV * 8), o_p1 = take(nV * 8),
-               o_q = take(nV * 8), o_rt = take(nV * 8), o_b = take(nV * 16),
+               o_cg = take(2 * 3 * nV * 16), o_rt = take(nV * 8), o_b = take(nV * 16),
                o_part = take((size_t)2 * h->grid * mreg::kRec * 4), o_bar = take(8),
                o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
                o_ih = take(kHistCap * 4), o_rh = take(kHistCap * 8),
@@ -568,11 +564,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->F = (float2*)(base + o_F);
   h->u0 = (float2*)(base + o_u0);
   h->hq = (float2*)(base + o_hq);
-  h->r = (float2*)(base + o_r);
-  h->z = (float2*)(base + o_z);
-  h->p0 = (float2*)(base + o_p0);
-  h->p1 = (float2*)(base + o_p1);
-  h->q = (float2*)(base + o_q);
+  h->cg = (float4*)(base + o_cg);
   h->rt = (float2*)(base + o_rt);
   h->b = (float4*)(base + o_b);
   h->part = (float*)(base + o_part);

@@ -55,11 +55,7 @@ struct IterArgs {
   float2* F;             // force, two buffers of nV (iteration parity)
   float2* u0;            // S0: u - tau F, two buffers of nV (iteration parity)
   float2* hq;            // edge form: per-edge force contribution
-  float2* r;             // CG residual (FP32)
-  float2* z;             // preconditioned residual
-  float2* p0;            // CG directions (ping-pong)
-  float2* p1;
-  float2* q;             // A p
+  float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s}
   float2* rt;            // true residual (FP32 copy) for restarts
   float4* b;             // right-hand side, float-float {x.hi, x.lo, y.hi, y.lo}
   // reductions / control
