@@ -88,6 +88,17 @@ enum {
                                    needs MREG_GRAD_SPLINE                    */
 };
 
+/* Where the iteration loop runs. */
+enum {
+  MREG_ENGINE_AUTO = 0,    /* the grid engine (measured faster on the 512^2 /
+                              20k-node workload)                              */
+  MREG_ENGINE_GRID = 1,    /* one persistent cooperative kernel over the GPU,
+                              node state in global memory (any mesh size)      */
+  MREG_ENGINE_CLUSTER = 2  /* one thread-block cluster (<= 16 CTAs) holding the
+                              node state in distributed shared memory (meshes
+                              up to ~26k nodes; not the edge-midpoint form)    */
+};
+
 typedef struct mreg_handle mreg_handle;
 
 /* Triangular mesh (V, T) of Sec. 2.1.  Host memory.
@@ -122,6 +133,7 @@ typedef struct {
   int32_t block_size;  /* threads per block of the iteration kernel (multiple of
                           32, <= 512); 0 = 256                              */
   int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
+  int32_t engine;      /* MREG_ENGINE_*                     (default AUTO)  */
 } mreg_options;
 
 typedef struct {
@@ -132,9 +144,11 @@ typedef struct {
   double last_rel_resid;       /* ||b - A u'|| / ||b|| (FP64) of the last
                                   solve, max over x and y                    */
   double last_energy;          /* data energy at the last sampled iterate    */
-  int32_t grid_blocks;         /* launch shape of the iteration kernel       */
+  int32_t grid_blocks;         /* launch shape of the iteration kernel (CTAs
+                                  of the cluster for the cluster engine)      */
   int32_t block_size;
   int32_t device_status;       /* raw device status bits (0 = clean)         */
+  int32_t engine;              /* MREG_ENGINE_GRID or MREG_ENGINE_CLUSTER     */
 } mreg_stats_t;
 
 /* Fields readable with mreg_get_field (mainly for parity tests). */

@@ -28,6 +28,8 @@ enum Form : int {
 // Everything the persistent iteration kernel reads or writes.
 struct IterArgs {
   int nV, nE, W, H, n_iters, it0, maxit, hist_cap;   // it0: history index of iteration 0
+  int chunk;             // cluster engine: nodes per CTA
+  float inv_chunk;       // 1 / chunk
   float tau, lam, area_floor, rtol2;
   float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
   // read-only mesh / operator data
@@ -95,6 +97,12 @@ cudaError_t launch_count_nonfinite(const float* img, int W, int H, int64_t strid
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
                             cudaStream_t s);
 int warp_grid_blocks(int W, int H, int num_sms);
+
+// Cluster engine (whole iteration state in the shared memory of one cluster).
+size_t cluster_smem_bytes(int form, int chunk);
+int cluster_block_size();
+cudaError_t cluster_prepare(int form, int grad, int C, int chunk, int* max_active);
+cudaError_t launch_cluster(int form, int grad, const IterArgs& a, int C, cudaStream_t s);
 
 // Iteration kernel: occupancy query and cooperative launch.
 cudaError_t iterate_max_blocks(int form, int grad, int block, int* max_blocks_per_sm);

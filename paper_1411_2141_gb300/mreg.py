@@ -55,6 +55,10 @@ MREG_FIELD_PCG_RESID = 9
 MODES = {"S0": MREG_MODE_EXPLICIT, "S1": MREG_MODE_UMBRELLA_IMPLICIT, "S2": MREG_MODE_FEM_IMPLICIT}
 GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
 QUADS = {"Q0": MREG_QUAD_NODES, "Q1": MREG_QUAD_EDGE_MIDPOINTS}
+MREG_ENGINE_AUTO = 0
+MREG_ENGINE_GRID = 1
+MREG_ENGINE_CLUSTER = 2
+ENGINES = {"auto": MREG_ENGINE_AUTO, "grid": MREG_ENGINE_GRID, "cluster": MREG_ENGINE_CLUSTER}
 
 
 class mreg_mesh(C.Structure):
@@ -70,7 +74,7 @@ class mreg_image(C.Structure):
 class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
-                ("block_size", C.c_int32), ("grid_blocks", C.c_int32)]
+                ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -78,7 +82,7 @@ class mreg_stats_t(C.Structure):
                 ("max_pcg_iters", C.c_int32), ("not_converged", C.c_int32),
                 ("last_rel_resid", C.c_double), ("last_energy", C.c_double),
                 ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
-                ("device_status", C.c_int32)]
+                ("device_status", C.c_int32), ("engine", C.c_int32)]
 
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
@@ -178,7 +182,7 @@ def default_options() -> mreg_options:
 
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
-                 block_size=0, grid_blocks=0) -> mreg_options:
+                 block_size=0, grid_blocks=0, engine="auto") -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -191,6 +195,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
         o.pcg_maxit = int(pcg_maxit)
     o.block_size = int(block_size)
     o.grid_blocks = int(grid_blocks)
+    o.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     return o
 
 

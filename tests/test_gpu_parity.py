@@ -25,6 +25,11 @@ U_TOL = 1e-4       # px
 MSD_RTOL = 1e-5
 MODES = [("S0", "G0", "Q0"), ("S0", "G1", "Q0"), ("S1", "G0", "Q0"), ("S1", "G1", "Q0"),
          ("S2", "G0", "Q0"), ("S2", "G1", "Q0"), ("S2", "G1", "Q1")]
+ENGINES = ["grid", "cluster"]
+
+
+def _engine_ok(engine, quad):
+    return not (engine == "cluster" and quad == "Q1")   # edge form runs on the grid engine
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -112,15 +117,19 @@ def test_pixel_map_bit_exact(mreg, c0, which):
     assert np.array_equal(got, ref.astype(np.int32))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("mode,grad,quad", MODES)
-def test_first_iteration_fields(mreg, c0, mode, grad, quad):
+def test_first_iteration_fields(mreg, c0, mode, grad, quad, engine):
+    if not _engine_ok(engine, quad):
+        pytest.skip("edge-midpoint form runs on the grid engine")
     pb = _oracle(c0, mode, grad, quad)
     u0 = np.zeros((pb.n, 2))
     f, rr, g = pb.sample(u0)
     F = pb.force(u0, f, rr, g)
     u1 = pb.update(u0, F)
     f1, _, _ = pb.sample(u1)   # TE_NODES describes the current u after the step
-    with _reg(mreg, c0, mode, grad, quad) as r:
+    with _reg(mreg, c0, mode, grad, quad, engine=engine) as r:
+        assert r.stats()["engine"] == mreg.ENGINES[engine]
         r.step(1)
         got_f = r.get_field(mreg.MREG_FIELD_TE_NODES)
         got_F = r.get_field(mreg.MREG_FIELD_FORCE)
@@ -134,12 +143,15 @@ def test_first_iteration_fields(mreg, c0, mode, grad, quad):
     assert abs(e[0] - pb.data_energy(u0)) <= 1e-5 * pb.data_energy(u0)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("mode,grad,quad", MODES)
-def test_registration_config0(mreg, c0, mode, grad, quad):
+def test_registration_config0(mreg, c0, mode, grad, quad, engine):
+    if not _engine_ok(engine, quad):
+        pytest.skip("edge-midpoint form runs on the grid engine")
     n = c0.spec.n_iter
     pb = _oracle(c0, mode, grad, quad)
     u_ref, e_ref = pb.run(n)
-    with _reg(mreg, c0, mode, grad, quad) as r:
+    with _reg(mreg, c0, mode, grad, quad, engine=engine) as r:
         r.step(n)
         u = r.get_u()
         msd = r.msd()
@@ -152,20 +164,22 @@ def test_registration_config0(mreg, c0, mode, grad, quad):
     msd_ref = pb.msd(u_ref)
     du = np.abs(u - u_ref).max()
     dm = abs(msd - msd_ref) / msd_ref
-    print(f"{mode}{grad}{quad}: du={du:.2e} dmsd={dm:.2e} its={st['max_pcg_iters']}")
+    print(f"{engine} {mode}{grad}{quad}: du={du:.2e} dmsd={dm:.2e} its={st['max_pcg_iters']}")
     assert du <= U_TOL
     assert dm <= MSD_RTOL
     np.testing.assert_allclose(e, e_ref, rtol=1e-5)
 
 
-@pytest.mark.parametrize("mode", ["S1", "S0"])
-def test_registration_config1_full_size(mreg, c1, mode):
-    """The 512^2 / 20k-node workload in the launch configuration the bench
-    times (automatic grid), full 200 iterations."""
+@pytest.mark.parametrize("mode,engine", [("S1", "auto"), ("S0", "auto"), ("S1", "cluster")])
+def test_registration_config1_full_size(mreg, c1, mode, engine):
+    """The 512^2 / 20k-node workload, full 200 iterations; "auto" is the
+    launch configuration the bench times (the grid engine)."""
     n = c1.spec.n_iter
     pb = _oracle(c1, mode)
     u_ref, _ = pb.run(n)
-    with _reg(mreg, c1, mode) as r:
+    with _reg(mreg, c1, mode, engine=engine) as r:
+        if engine == "auto":
+            assert r.stats()["engine"] == mreg.MREG_ENGINE_GRID
         r.step(n)
         u = r.get_u()
         msd = r.msd()
@@ -173,7 +187,7 @@ def test_registration_config1_full_size(mreg, c1, mode):
     msd_ref = pb.msd(u_ref)
     du = np.abs(u - u_ref).max()
     dm = abs(msd - msd_ref) / msd_ref
-    print(f"c1 {mode}: du={du:.2e} dmsd={dm:.2e}")
+    print(f"c1 {mode} {engine}: du={du:.2e} dmsd={dm:.2e}")
     assert du <= U_TOL
     assert dm <= MSD_RTOL
 
@@ -201,10 +215,11 @@ def test_msd_at_zero_displacement_is_pixel_mean(mreg, c0):
     assert abs(m - ref) <= 1e-6 * ref
 
 
-def test_runs_are_bitwise_repeatable(mreg, c0):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_runs_are_bitwise_repeatable(mreg, c0, engine):
     outs = []
     for _ in range(2):
-        with _reg(mreg, c0, "S1") as r:
+        with _reg(mreg, c0, "S1", engine=engine) as r:
             r.step(30)
             outs.append((r.get_u(), r.msd()))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -237,11 +252,20 @@ def test_reset_restarts_the_registration(mreg, c0):
 def test_launch_shape_changes_only_rounding(mreg, c0):
     res = []
     for grid in (0, 3, 17):
-        with _reg(mreg, c0, "S1", grid_blocks=grid, block_size=128) as r:
+        with _reg(mreg, c0, "S1", grid_blocks=grid, block_size=128, engine="grid") as r:
             r.step(30)
             res.append(r.get_u())
+    with _reg(mreg, c0, "S1", engine="cluster") as r:
+        r.step(30)
+        res.append(r.get_u())
     for u in res[1:]:
         assert np.abs(u - res[0]).max() <= 1e-5
+
+
+def test_cluster_engine_rejects_edge_form(mreg, c0):
+    with pytest.raises(mreg.MregError) as e:
+        _reg(mreg, c0, "S2", "G1", "Q1", engine="cluster")
+    assert e.value.status == mreg.MREG_ERR_INVALID_ARG
 
 
 def test_device_images_with_row_stride(mreg, c0):
