@@ -43,7 +43,7 @@ mreg_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr int kHistCap = 4096;
-constexpr int kChunk = 4096;   // iterations per launch of the iteration kernel
+constexpr int kChunk = 1024;   // iterations per launch of the iteration kernel
 constexpr int kMaxPcgIt = 10000;
 constexpr double kDegenerateRel = 1e-12;
 
@@ -272,6 +272,7 @@ struct mreg_handle {
   int* status = nullptr;
   double* last = nullptr;
   double* energy_hist = nullptr;
+  float2* epart = nullptr;   // grid engine: per-warp energy partials of one launch
   int* pcg_it_hist = nullptr;
   double* pcg_res_hist = nullptr;
   float* warp_part = nullptr;
@@ -325,6 +326,8 @@ struct mreg_handle {
     a.bar = bar;
     a.status = status;
     a.energy_hist = energy_hist;
+    a.epart = epart;
+    a.ewarps = (grid * block + 31) / 32;
     a.pcg_it_hist = pcg_it_hist;
     a.pcg_res_hist = pcg_res_hist;
     a.last = last;
@@ -569,7 +572,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_part = take((size_t)2 * h->grid * mreg::kRec * 4), o_bar = take(8),
                o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
                o_ih = take(kHistCap * 4), o_rh = take(kHistCap * 8),
-               o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16);
+               o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16),
+               o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8);
   CK(cudaMalloc(&h->arena, off), "device allocation");
   char* base = (char*)h->arena;
   h->Re = (float*)(base + o_Re);
@@ -613,6 +617,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->warp_part = (float*)(base + o_wp);
   h->msd = (double*)(base + o_msd);
   h->counters = (int*)(base + o_cnt);
+  h->epart = (float2*)(base + o_ep);
 
   st = upload_image(h, Re, h->Re, s, "Re");
   if (st) return st;

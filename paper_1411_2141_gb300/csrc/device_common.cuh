@@ -144,26 +144,34 @@ struct GridBarrier {
   unsigned long long nblocks;
   unsigned long long epoch;
 
-  // Returns false (block-uniformly) when the kernel must stop.
+  // Returns false (block-uniformly) when the kernel must stop.  The wait is a
+  // bare acquire-load loop; the abort flag and the clock are looked at only
+  // every 32 polls, since they matter only when something went wrong.
   __device__ __forceinline__ bool sync(int* s_flag) {
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
       red_release_add(counter, 1ull);
       const unsigned long long target = epoch * nblocks;
-      const uint64_t t0 = global_ns();
-      int st = 0;
-      while (true) {
-        if (ld_acquire_u64(counter) >= target) break;
-        st = ld_volatile_i32(status);
-        if (st & kStatusAbort) break;
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
-          atomicOr(status, kStatusBarrierTimeout | kStatusAbort);
-          break;
+      int flag = 0;
+      if (ld_acquire_u64(counter) < target) {
+        const uint64_t t0 = global_ns();
+        for (unsigned spin = 1;; ++spin) {
+          if (ld_acquire_u64(counter) >= target) break;
+          if ((spin & 31u) == 0) {
+            if (ld_volatile_i32(status) & kStatusAbort) {
+              flag = 1;
+              break;
+            }
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+              atomicOr(status, kStatusBarrierTimeout | kStatusAbort);
+              flag = 1;
+              break;
+            }
+          }
         }
       }
-      __threadfence();
-      *s_flag = ld_volatile_i32(status) & kStatusAbort;
+      *s_flag = flag;
     }
     __syncthreads();
     return *s_flag == 0;
@@ -237,6 +245,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 __device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
 
 __device__ __forceinline__ ff ff_load(float2 v) { return ff{v.x, v.y}; }
+
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff d_to_ff(double d) {
+  const float hi = (float)d;
+  return ff{hi, (float)(d - (double)hi)};
+}
 
 __device__ __forceinline__ ff ff_shfl_xor(ff a, int off) {
   return ff{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
@@ -330,6 +344,146 @@ __device__ __forceinline__ void grid_reduce(const float* part, int nblocks, floa
   for (int k = 0; k < NF; ++k) tot[k] = s_red[k];
   if (E) etot = ff{s_red[NF], s_red[NF + 1]};
   __syncthreads();
+}
+
+// Totals over all block records (call after a grid barrier), in one warp:
+// lane l takes the records of blocks l, l+32, ... (issuing their loads
+// together), then a butterfly adds the lanes.  The assignment and the order
+// are fixed, so every block obtains bitwise the same totals.
+template <int NF, bool E>
+__device__ __forceinline__ void grid_reduce_w0(const float* part, int nblocks, float (&tot)[NF],
+                                               ff& etot, float* s_tot) {
+  constexpr int kW = NF + (E ? 2 : 0);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float v[NF];
+    ff e = ff_zero();
+#pragma unroll
+    for (int k = 0; k < NF; ++k) v[k] = 0.0f;
+    for (int b0 = lane; b0 < nblocks; b0 += 4 * 32) {
+      float rr[4][kW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + 32 * u;
+        if (b < nblocks) {
+#pragma unroll
+          for (int k = 0; k < kW; ++k) rr[u][k] = __ldcg(part + (size_t)b * kRec + k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kW; ++k) rr[u][k] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) v[k] += rr[u][k];
+        if (E) e = ff_add(e, ff{rr[u][NF], rr[u][NF + 1]});
+      }
+    }
+    warp_sums<NF, E>(v, e);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k) s_tot[k] = v[k];
+      if (E) {
+        s_tot[NF] = e.hi;
+        s_tot[NF + 1] = e.lo;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NF; ++k) tot[k] = s_tot[k];
+  if (E) etot = ff{s_tot[NF], s_tot[NF + 1]};
+  __syncthreads();
+}
+
+// Store the warp's float-float total of e at slot[warp_id] (lane 0 writes):
+// the energy is summed over warps after the launch (it does not steer the
+// iteration), which keeps float-float additions off the per-phase path.
+__device__ __forceinline__ void warp_energy_store(ff e, float2* slot, int warp_id) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e = ff_add(e, ff_shfl_xor(e, off));
+  if ((threadIdx.x & 31) == 0) slot[warp_id] = make_float2(e.hi, e.lo);
+}
+
+// Block reduction with one __syncthreads: every warp's lane 0 leaves its warp
+// total in s_red; warp 0 then adds the warps in order, slot by slot, and
+// stores this block's record rec[0 .. NF+2).  The barrier that follows
+// orders the record for the other blocks.  s_red must not be reused before
+// the next __syncthreads (the grid barrier has one).
+template <int NF, bool E>
+__device__ __forceinline__ void block_record(float (&v)[NF], ff e, float* rec, float* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sums<NF, E>(v, e);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) s_red[warp * kRec + k] = v[k];
+    if (E) {
+      s_red[warp * kRec + NF] = e.hi;
+      s_red[warp * kRec + NF + 1] = e.lo;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    if (lane < NF) {
+      float t = 0.0f;
+      for (int w = 0; w < nw; ++w) t += s_red[w * kRec + lane];
+      rec[lane] = t;
+    } else if (E && lane == NF) {
+      ff t = ff_zero();
+      for (int w = 0; w < nw; ++w) t = ff_add(t, ff{s_red[w * kRec + NF], s_red[w * kRec + NF + 1]});
+      rec[NF] = t.hi;
+      rec[NF + 1] = t.lo;
+    }
+  }
+}
+
+// Totals over all block records (call after a grid barrier): warp 0 reads
+// the records (lane l takes blocks l, l+32, ... in order, loads issued
+// together), adds the lanes by a butterfly and leaves the totals in s_tot;
+// one __syncthreads publishes them to the block.  s_tot must alternate
+// between two buffers from one reduction to the next.  Every block obtains
+// bitwise the same totals.
+template <int NF, bool E>
+__device__ __forceinline__ void grid_totals(const float* part, int nblocks, float (&tot)[NF],
+                                            ff& etot, float* s_tot) {
+  constexpr int kW = NF + (E ? 2 : 0);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float v[NF];
+    ff e = ff_zero();
+#pragma unroll
+    for (int k = 0; k < NF; ++k) v[k] = 0.0f;
+    for (int b0 = lane; b0 < nblocks; b0 += 4 * 32) {
+      float rr[4][kW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + 32 * u;
+#pragma unroll
+        for (int k = 0; k < kW; ++k) rr[u][k] = b < nblocks ? __ldcg(part + (size_t)b * kRec + k) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) v[k] += rr[u][k];
+        if (E) e = ff_add(e, ff{rr[u][NF], rr[u][NF + 1]});
+      }
+    }
+    warp_sums<NF, E>(v, e);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k) s_tot[k] = v[k];
+      if (E) {
+        s_tot[NF] = e.hi;
+        s_tot[NF + 1] = e.lo;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NF; ++k) tot[k] = s_tot[k];
+  if (E) etot = ff{s_tot[NF], s_tot[NF + 1]};
 }
 
 }  // namespace mreg

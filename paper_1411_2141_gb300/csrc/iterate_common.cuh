@@ -164,18 +164,42 @@ struct CgNext {
   float2 p, s, r, z, x;
 };
 
-__device__ __forceinline__ CgNext cg_next(const Cg& c, float dinv, const CgStep& k) {
-  CgNext n;
+// The z-part of cg_next: needs r, w, s only.
+struct CgNextZ {
+  float2 s, r, z;
+};
+__device__ __forceinline__ CgNextZ cg_next_z(float2 r, float2 w, float2 s, float dinv,
+                                             const CgStep& k) {
+  CgNextZ n;
   if (k.first) {
-    n.p = c.z;
-    n.s = c.w;
+    n.s = w;
   } else {
-    n.p = make_float2(__fmaf_rn(k.beta.x, c.p.x, c.z.x), __fmaf_rn(k.beta.y, c.p.y, c.z.y));
-    n.s = make_float2(__fmaf_rn(k.beta.x, c.s.x, c.w.x), __fmaf_rn(k.beta.y, c.s.y, c.w.y));
+    n.s = make_float2(__fmaf_rn(k.beta.x, s.x, w.x), __fmaf_rn(k.beta.y, s.y, w.y));
   }
-  n.r = make_float2(__fmaf_rn(-k.alpha.x, n.s.x, c.r.x), __fmaf_rn(-k.alpha.y, n.s.y, c.r.y));
+  n.r = make_float2(__fmaf_rn(-k.alpha.x, n.s.x, r.x), __fmaf_rn(-k.alpha.y, n.s.y, r.y));
   n.z = make_float2(__fmul_rn(dinv, n.r.x), __fmul_rn(dinv, n.r.y));
-  n.x = make_float2(__fmaf_rn(k.alpha.x, n.p.x, c.x.x), __fmaf_rn(k.alpha.y, n.p.y, c.x.y));
+  return n;
+}
+// The x-part of cg_next: needs x, z, p only.
+__device__ __forceinline__ float2 cg_next_x(float2 x, float2 z, float2 p, const CgStep& k,
+                                            float2* pn) {
+  float2 pp;
+  if (k.first) {
+    pp = z;
+  } else {
+    pp = make_float2(__fmaf_rn(k.beta.x, p.x, z.x), __fmaf_rn(k.beta.y, p.y, z.y));
+  }
+  if (pn) *pn = pp;
+  return make_float2(__fmaf_rn(k.alpha.x, pp.x, x.x), __fmaf_rn(k.alpha.y, pp.y, x.y));
+}
+
+__device__ __forceinline__ CgNext cg_next(const Cg& c, float dinv, const CgStep& k) {
+  const CgNextZ nz = cg_next_z(c.r, c.w, c.s, dinv, k);
+  CgNext n;
+  n.s = nz.s;
+  n.r = nz.r;
+  n.z = nz.z;
+  n.x = cg_next_x(c.x, c.z, c.p, k, &n.p);
   return n;
 }
 

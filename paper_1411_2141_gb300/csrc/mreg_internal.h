@@ -65,6 +65,8 @@ struct IterArgs {
   unsigned long long* bar;  // barrier counter (zeroed before each launch)
   int* status;           // device status bits
   double* energy_hist;   // per-iteration data energy (hist_cap entries)
+  float2* epart;         // grid engine: per-warp energy partials, (n_iters + 1) x ewarps
+  int ewarps;            // warps of the grid-engine launch
   int* pcg_it_hist;
   double* pcg_res_hist;
   double* last;          // [0] last energy, [1] last rel. residual, [2] last CG its,

@@ -111,12 +111,12 @@ __global__ void __launch_bounds__(kWarpBlock) k_warp_msd(const WarpArgs a) {
 __global__ void k_msd_final(const float* __restrict__ part, int nb, double inv_count,
                             double* __restrict__ out) {
   const int lane = threadIdx.x;
-  ff s = ff_zero();
+  double s = 0.0;
   for (int b = lane; b < nb; b += 32)
-    s = ff_add(s, ff{part[(size_t)b * kRec + 1], part[(size_t)b * kRec + 2]});
+    s += ff_to_d(ff{part[(size_t)b * kRec + 1], part[(size_t)b * kRec + 2]});
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s = ff_add(s, ff_shfl_xor(s, off));
-  if (lane == 0) *out = ((double)s.hi + (double)s.lo) * inv_count;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) *out = s * inv_count;
 }
 
 }  // namespace
