@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--config", type=int, default=1)
     p.add_argument("--mode", default="S1", choices=["S0", "S1", "S2"])
     p.add_argument("--grad", default="G0", choices=["G0", "G1"])
+    p.add_argument("--coeff", default="fp32", choices=["fp32", "bf16"],
+                   help="storage of Te's spline coefficients (bf16: the precision form)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -166,13 +168,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def launches_per_registration(args, n_iter: int) -> int:
+    """Our kernels in one timed step: prefilter (row and column pass) of Re
+    and Te, [BF16 copy], Re at the nodes, [Re at edge midpoints], pixel map
+    (fill + scan), the persistent iteration kernel and its energy pass per
+    1024-iteration chunk, warp + MSD and the final MSD sum."""
+    chunks = (n_iter + 1023) // 1024
+    return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 2)
+
+
 def workload_config(args, case):
     s = case.spec
     return {"workload": f"config{args.config}: {s.side}x{s.side} pair, {case.n_nodes}-node mesh, "
                         f"{s.n_iter} iterations, {args.mode} {MODE_NAMES[args.mode]}, "
-                        f"{args.grad} {'mesh gradient Eq.9-10' if args.grad == 'G0' else 'spline gradient'}",
+                        f"{args.grad} {'mesh gradient Eq.9-10' if args.grad == 'G0' else 'spline gradient'}"
+                        + (", BF16-stored Te coefficients" if args.coeff == "bf16" else ""),
             "image": [s.side, s.side], "nodes": case.n_nodes, "triangles": case.n_tris,
-            "iterations": s.n_iter, "mode": args.mode, "grad": args.grad,
+            "iterations": s.n_iter, "mode": args.mode, "grad": args.grad, "coeff": args.coeff,
             "alpha": s.alpha, "tau": s.tau,
             "l2": "flushed between timed steps (256 MiB write); the step's own working set is L2-resident",
             "parallelism": f"replicas x{args.gpus} (one pair per GPU per step)"}
@@ -192,8 +204,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     Re_d = torch.from_numpy(case.Re).to(dev)
     Te_d = torch.from_numpy(case.Te).to(dev)
+    bf16 = args.coeff == "bf16"
     reg = mreg.Registration(case.V, case.T, Re_d, Te_d, spec.alpha, spec.tau,
-                            mode=args.mode, grad=args.grad, stream=stream)
+                            mode=args.mode, grad=args.grad, coeff_bf16=bf16, stream=stream)
     msd_dev = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -252,7 +265,8 @@ def run_ours(args, rank, world, local_rank):
 
         def e2e_once():
             with mreg.Registration(case.V, case.T, Re_h, Te_h, spec.alpha, spec.tau,
-                                   mode=args.mode, grad=args.grad, stream=stream) as r:
+                                   mode=args.mode, grad=args.grad, coeff_bf16=bf16,
+                                   stream=stream) as r:
                 r.step(n_iter, stream)
                 m = r.msd(stream)
                 u = r.get_u(stream=stream)
@@ -306,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": per_iter * n_iter,
                      "traffic": None},
         "clocks": clk,
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": launches_per_registration(args, n_iter) * args.steps,
         "launch": {"grid": st["grid_blocks"], "block": st["block_size"]},
     }
     if e2e is not None:

@@ -134,6 +134,13 @@ typedef struct {
                           32, <= 512); 0 = 256                              */
   int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
   int32_t engine;      /* MREG_ENGINE_*                     (default AUTO)  */
+  int32_t coeff_bf16;  /* 1: the iteration and the warp read Te's B-spline
+                          coefficients from a BF16 copy (round to nearest
+                          even of the FP32 prefilter output); every sum and
+                          product stays FP32 and the reductions keep their
+                          precision.  Halves the coefficient footprint; the
+                          error this adds is stated against the FP64 method,
+                          not bounded by the FP32 tolerances.  (default 0)  */
 } mreg_options;
 
 typedef struct {
@@ -166,8 +173,11 @@ enum {
                                 last mreg_step call                           */
   MREG_FIELD_PCG_ITERS = 8,  /* n int32: CG iterations of each iteration of
                                 the last mreg_step call                       */
-  MREG_FIELD_PCG_RESID = 9   /* n double: final relative FP64 residual of each
+  MREG_FIELD_PCG_RESID = 9,  /* n double: final relative FP64 residual of each
                                 solve of the last mreg_step call              */
+  MREG_FIELD_COEF_TE_BF16 = 10 /* H x W uint16: the BF16 copy of Te's
+                                coefficients (bit patterns); 0 elements when
+                                coeff_bf16 is off                             */
 };
 
 /* Fill *opts with the defaults listed in mreg_options. */

@@ -254,6 +254,7 @@ struct mreg_handle {
   void* arena = nullptr;
   // device arrays
   float *Re = nullptr, *Te = nullptr, *cRe = nullptr, *cTe = nullptr, *tmp = nullptr;
+  __nv_bfloat16* cTe16 = nullptr;   // BF16 copy of cTe (coeff_bf16 only)
   int* pix_tri = nullptr;
   float2* V = nullptr;
   int *tri = nullptr, *inc_ptr = nullptr;
@@ -312,6 +313,7 @@ struct mreg_handle {
     a.dinv = dinv;
     a.lumped = lumped;
     a.cTe = cTe;
+    a.cTe16 = cTe16;
     a.ReV = ReV;
     a.ReQ = ReQ;
     a.u = u;
@@ -387,6 +389,8 @@ mreg_status upload_image(mreg_handle* h, const mreg_image* im, float* dst, cudaS
 mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
   CK(mreg::launch_prefilter(h->Re, h->W, h->tmp, h->cRe, h->W, h->H, s), "prefilter Re");
   CK(mreg::launch_prefilter(h->Te, h->W, h->tmp, h->cTe, h->W, h->H, s), "prefilter Te");
+  if (h->cTe16)
+    CK(mreg::launch_to_bf16(h->cTe, (int64_t)h->W * h->H, h->cTe16, s), "BF16 coefficients");
   CK(mreg::launch_sample_nodes(h->cRe, h->W, h->H, h->V, h->nV, h->ReV, s), "Re at nodes");
   if (h->form == mreg::kFormFemEdges)
     CK(mreg::launch_sample_edges(h->cRe, h->W, h->H, h->V, h->edges, h->nE, h->ReQ, s),
@@ -464,6 +468,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
     return fail(MREG_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
   if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
   if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
+  if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
+    return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
   const double lam = o.lambda < 0.0 ? tau * alpha : o.lambda;
   if (!std::isfinite(lam)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
 
@@ -573,7 +579,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
                o_ih = take(kHistCap * 4), o_rh = take(kHistCap * 8),
                o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16),
-               o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8);
+               o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8),
+               o_c16 = take(o.coeff_bf16 ? npx * 2 : 0);
   CK(cudaMalloc(&h->arena, off), "device allocation");
   char* base = (char*)h->arena;
   h->Re = (float*)(base + o_Re);
@@ -618,6 +625,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->msd = (double*)(base + o_msd);
   h->counters = (int*)(base + o_cnt);
   h->epart = (float2*)(base + o_ep);
+  h->cTe16 = o.coeff_bf16 ? (__nv_bfloat16*)(base + o_c16) : nullptr;
 
   st = upload_image(h, Re, h->Re, s, "Re");
   if (st) return st;
@@ -690,6 +698,7 @@ mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* str
   a.pix_tri = h->pix_tri;
   a.u = h->u;
   a.cTe = h->cTe;
+  a.cTe16 = h->cTe16;
   a.Re = h->Re;
   a.out = out_dev;
   a.part = h->warp_part;
@@ -762,6 +771,7 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
     case MREG_FIELD_ENERGY: src = h->energy_hist, count = hist, esize = 8; break;
     case MREG_FIELD_PCG_ITERS: src = h->pcg_it_hist, count = hist; break;
     case MREG_FIELD_PCG_RESID: src = h->pcg_res_hist, count = hist, esize = 8; break;
+    case MREG_FIELD_COEF_TE_BF16: src = h->cTe16, count = h->cTe16 ? npx : 0, esize = 2; break;
     default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
   }
   if (count_out) *count_out = count;

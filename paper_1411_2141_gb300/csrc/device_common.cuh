@@ -3,6 +3,7 @@
 // iteration kernel, and deterministic (fixed-order) FP64 reductions.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,12 +44,19 @@ __device__ __forceinline__ void cubic_dweights(float t, float d[4]) {
   d[3] = 0.5f * t2;
 }
 
+// Coefficient loads: FP32, or BF16 storage widened exactly to FP32 (all the
+// arithmetic stays FP32).
+__device__ __forceinline__ float load_coef(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_coef(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+
 // Spline value at the point (bx + ox, by + oy) of a dense W x H coefficient
 // image.  The integer base and the (small) float offset are kept apart so
 // the position keeps ~1e-6 px precision at any image size.  With GRAD the
 // partial derivatives are returned as well.
-template <bool GRAD>
-__device__ __forceinline__ float spline_sample(const float* __restrict__ c, int W, int H,
+template <bool GRAD, class C = float>
+__device__ __forceinline__ float spline_sample(const C* __restrict__ c, int W, int H,
                                                int bx, int by, float ox, float oy,
                                                float* gx, float* gy) {
   // A non-finite or huge offset (a diverged iterate) is clamped so that the
@@ -84,9 +92,9 @@ __device__ __forceinline__ float spline_sample(const float* __restrict__ c, int 
   float v = 0.0f, ax = 0.0f, ay = 0.0f;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    const float* row = c + (size_t)ys[m] * W;
-    const float c0 = __ldg(row + xs[0]), c1 = __ldg(row + xs[1]);
-    const float c2 = __ldg(row + xs[2]), c3 = __ldg(row + xs[3]);
+    const C* row = c + (size_t)ys[m] * W;
+    const float c0 = load_coef(row + xs[0]), c1 = load_coef(row + xs[1]);
+    const float c2 = load_coef(row + xs[2]), c3 = load_coef(row + xs[3]);
     const float sx = wx[0] * c0 + wx[1] * c1 + wx[2] * c2 + wx[3] * c3;
     v += wy[m] * sx;
     if (GRAD) {

@@ -2,6 +2,7 @@
 // blocks and the kernel launchers (one per hot-path step).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,6 +50,7 @@ struct IterArgs {
   const float* dinv;     // 1 / diag(A), Jacobi preconditioner (S1, S2)
   const float* lumped;   // FEM nodal quadrature weight A(V_a)/3
   const float* cTe;      // B-spline coefficients of Te, dense W x H
+  const __nv_bfloat16* cTe16;   // BF16 copy of cTe read instead when non-null
   const float* ReV;      // Re at the undeformed nodes
   const float* ReQ;      // Re at the undeformed edge midpoints
   // mutable state
@@ -80,6 +82,7 @@ struct WarpArgs {
   const int* pix_tri;
   const float2* u;
   const float* cTe;
+  const __nv_bfloat16* cTe16;   // BF16 copy of cTe read instead when non-null
   const float* Re;       // dense W x H reference pixels
   float* out;            // optional registered image
   float* part;           // one reduction record (kRec floats) per block
@@ -94,6 +97,7 @@ cudaError_t launch_sample_edges(const float* coef, int W, int H, const float2* V
                                 const int2* edges, int nE, float* out, cudaStream_t s);
 cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int H, int* pix_tri,
                              int* uncovered, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s);
 cudaError_t launch_count_nonfinite(const float* img, int W, int H, int64_t stride, int* count,
                                    cudaStream_t s);
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kWarpBlock) k_warp_msd(const WarpArgs a) {
     const float inv = 1.0f / (sa + sb + sc);
     const float ux = (sa * ua.x + sb * ub.x + sc * uc.x) * inv;
     const float uy = (sa * ua.y + sb * ub.y + sc * uc.y) * inv;
-    const float R = spline_sample<false>(a.cTe, W, H, x, y, ux, uy, nullptr, nullptr);
+    const float R = a.cTe16 ? spline_sample<false>(a.cTe16, W, H, x, y, ux, uy, nullptr, nullptr)
+                            : spline_sample<false>(a.cTe, W, H, x, y, ux, uy, nullptr, nullptr);
     if (a.out) a.out[p] = R;
     const float d = R - __ldg(a.Re + p);
     acc = ff_add(acc, ff_prod(d, d));

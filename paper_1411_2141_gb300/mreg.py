@@ -51,6 +51,7 @@ MREG_FIELD_PIXEL_TRI = 6
 MREG_FIELD_ENERGY = 7
 MREG_FIELD_PCG_ITERS = 8
 MREG_FIELD_PCG_RESID = 9
+MREG_FIELD_COEF_TE_BF16 = 10
 
 MODES = {"S0": MREG_MODE_EXPLICIT, "S1": MREG_MODE_UMBRELLA_IMPLICIT, "S2": MREG_MODE_FEM_IMPLICIT}
 GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
@@ -74,7 +75,8 @@ class mreg_image(C.Structure):
 class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
-                ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32)]
+                ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
+                ("coeff_bf16", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -182,7 +184,8 @@ def default_options() -> mreg_options:
 
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
-                 block_size=0, grid_blocks=0, engine="auto") -> mreg_options:
+                 block_size=0, grid_blocks=0, engine="auto",
+                 coeff_bf16=False) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -196,6 +199,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.block_size = int(block_size)
     o.grid_blocks = int(grid_blocks)
     o.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    o.coeff_bf16 = int(bool(coeff_bf16))
     return o
 
 
@@ -314,14 +318,16 @@ class Registration:
         _check(lib.mreg_get_field(self._h, field, None, 0, C.byref(n), _stream_ptr(stream)),
                "mreg_get_field")
         dtype = {MREG_FIELD_PIXEL_TRI: np.int32, MREG_FIELD_PCG_ITERS: np.int32,
-                 MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64}.get(field, np.float32)
+                 MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64,
+                 MREG_FIELD_COEF_TE_BF16: np.uint16}.get(field, np.float32)
         out = np.empty(n.value, dtype)
         if n.value:
             _check(lib.mreg_get_field(self._h, field, out.ctypes.data, 0, None, _stream_ptr(stream)),
                    "mreg_get_field")
         if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
             out = out.reshape(-1, 2)
-        elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI):
+        elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
+                field == MREG_FIELD_COEF_TE_BF16 and n.value):
             out = out.reshape(self.height, self.width)
         return out
 

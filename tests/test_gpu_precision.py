@@ -1,0 +1,118 @@
+"""The precision form: BF16-stored coefficients of Te, and the 2048^2 pair.
+
+With ``coeff_bf16`` the iteration and the warp read Te's B-spline
+coefficients from a BF16 copy; all arithmetic stays FP32 and the FP64
+reductions are unchanged.  Its error is measured against the FP64 oracle and
+must stay within 1e-2 px; the FP32 form keeps the 1e-4 px / 1e-5 MSD bar at
+every size, including the 2048^2 image with the ~250k-node mesh.
+
+Tolerance of the stored copy: round to nearest even keeps 8 significant
+bits, so |bf16(c) - c| <= 2^-9 |c| (rounded up to 2^-8 to cover the FP32
+prefilter's own error of a few ulps).
+"""
+import numpy as np
+import pytest
+
+from oracle import register
+from paper_1411_2141_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U_TOL = 1e-4       # px, FP32 form
+MSD_RTOL = 1e-5
+U_TOL_BF16 = 1e-2  # px, BF16-stored coefficients
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_2141_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def mreg():
+    from paper_1411_2141_gb300 import mreg as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def c0():
+    return inputs.make_case(inputs.config_spec(0))
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return inputs.make_case(inputs.config_spec(2))
+
+
+def _reg(mreg, case, mode="S1", grad="G0", **kw):
+    return mreg.Registration(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
+                             mode=mode, grad=grad, **kw)
+
+
+def _oracle(case, mode="S1", grad="G0"):
+    return register.Problem(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
+                            mode, grad)
+
+
+def _bf16_to_f64(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_bf16_copy_of_coefficients(mreg, c0):
+    pb = _oracle(c0)
+    with _reg(mreg, c0, coeff_bf16=True) as r:
+        c16 = _bf16_to_f64(r.get_field(mreg.MREG_FIELD_COEF_TE_BF16))
+    assert c16.shape == pb.cTe.shape
+    err = np.abs(c16 - pb.cTe)
+    assert (err <= 2.0 ** -8 * np.abs(pb.cTe) + 5e-6 * np.abs(pb.cTe).max()).all()
+    with _reg(mreg, c0) as r:   # the FP32 form keeps no copy
+        assert r.get_field(mreg.MREG_FIELD_COEF_TE_BF16).size == 0
+
+
+@pytest.mark.parametrize("mode,grad", [("S0", "G0"), ("S1", "G0"), ("S2", "G1")])
+def test_bf16_registration_config0(mreg, c0, mode, grad):
+    n = c0.spec.n_iter
+    pb = _oracle(c0, mode, grad)
+    u_ref, _ = pb.run(n)
+    msd_ref = pb.msd(u_ref)
+    with _reg(mreg, c0, mode, grad, coeff_bf16=True) as r:
+        r.step(n)
+        u = r.get_u()
+        msd = r.msd()
+        r.stats()
+    du = np.abs(u - u_ref).max()
+    dm = abs(msd - msd_ref) / msd_ref
+    print(f"bf16 c0 {mode}{grad}: du={du:.2e} px dmsd={dm:.2e}")
+    assert du <= U_TOL_BF16
+
+
+def test_config2_full_size(mreg, c2):
+    """The 2048^2 / 250k-node pair: FP32 form to the FP32 bar, BF16 form to
+    its stated bound, both against the same FP64 oracle trajectory (20 of the
+    300 iterations, to keep the oracle in seconds)."""
+    n = 20
+    pb = _oracle(c2)
+    u_ref, e_ref = pb.run(n)
+    msd_ref = pb.msd(u_ref)
+    out = {}
+    for bf16 in (False, True):
+        with _reg(mreg, c2, coeff_bf16=bf16) as r:
+            assert r.stats()["engine"] == mreg.MREG_ENGINE_GRID
+            r.step(n)
+            u = r.get_u()
+            msd = r.msd()
+            e = r.get_field(mreg.MREG_FIELD_ENERGY)
+            r.stats()
+        out[bf16] = (np.abs(u - u_ref).max(), abs(msd - msd_ref) / msd_ref, e)
+        print(f"c2 S1G0 bf16={bf16}: du={out[bf16][0]:.2e} px dmsd={out[bf16][1]:.2e}")
+    du, dm, e = out[False]
+    assert du <= U_TOL
+    assert dm <= MSD_RTOL
+    np.testing.assert_allclose(e, e_ref, rtol=1e-5)
+    assert out[True][0] <= U_TOL_BF16
