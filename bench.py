@@ -9,6 +9,11 @@ Metric: registrations/s (and node-iterations/s).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--mode S1] [--config 1]
 
+--config 3 times the batched form instead: one step registers 256 pairs of
+uneven size (sides 96-768, 500-40k nodes, 100 iterations each) in one CUDA
+graph launch around one persistent kernel, with the team shape chosen by the
+library's autotuner before timing.
+
 --impl reference times the FP64 CPU oracle on the host cores instead (a
 bounded sample of each registration, extrapolated to the full iteration
 count).  Under torchrun (N > 1) every rank registers its own pairs on its
@@ -142,6 +147,8 @@ def oracle_registration_time(case, mode: str, grad: str, sample_iters: int = 20)
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.config == 3:
+        return run_reference_batch(args)
     spec = inputs.config_spec(args.config)
     case = inputs.make_case(spec)
     for _ in range(args.warmup):
@@ -177,6 +184,34 @@ def launches_per_registration(args, n_iter: int) -> int:
     return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 2)
 
 
+def run_reference_batch(args):
+    cases = batch_cases()
+    n_iter = cases[0].spec.n_iter
+    for _ in range(args.warmup):
+        oracle_registration_time(cases[0], args.mode, args.grad, sample_iters=2)
+    total, pick, si = 0.0, None, None
+    for _ in range(args.steps):
+        t, pick, si = oracle_batch_time(cases, args.mode, args.grad, n_sample_pairs=4,
+                                        sample_iters=5)
+        total += t
+    value = args.steps * len(cases) / total
+    sample = (f"per step: {len(pick)} of {len(cases)} pairs spread over the size range, set-up + "
+              f"{si} of {n_iter} iterations (scaled x{n_iter / si:g}) + MSD each, scaled to the "
+              f"batch by node count")
+    line = {
+        "impl": "reference", "metric": "registrations/s", "value": value, "unit": "registrations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batch_workload_config(args, cases),
+        "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(args, case):
     s = case.spec
     return {"workload": f"config{args.config}: {s.side}x{s.side} pair, {case.n_nodes}-node mesh, "
@@ -188,6 +223,30 @@ def workload_config(args, case):
             "alpha": s.alpha, "tau": s.tau,
             "l2": "flushed between timed steps (256 MiB write); the step's own working set is L2-resident",
             "parallelism": f"replicas x{args.gpus} (one pair per GPU per step)"}
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (x itself when world == 1)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units of all ranks per second of the slowest rank (weak scaling)."""
+    return units_per_rank * world / seconds
+
+
+def peak_hbm():
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        with open(pk_path) as fh:
+            peaks = json.load(fh)
+    return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
 
 
 # --------------------------------------------------------------- GPU side
@@ -247,11 +306,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     iter_ms = [a.elapsed_time(b) for a, b in it_ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     msd = float(msd_dev.item())
     st = reg.stats(stream)
 
@@ -279,31 +334,22 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(e2e_steps):
             e2e_once()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = case.Re.nbytes + case.Te.nbytes + case.V.nbytes + case.T.nbytes
         d2h = 8 + case.V.nbytes
-        e2e = {"value": e2e_steps * world / e2e_s, "unit": "registrations/s",
+        e2e = {"value": whole_job_rate(e2e_steps, world, e2e_s), "unit": "registrations/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": e2e_steps}
 
     if rank != 0:
         return
-    value = args.steps * world / total_s
+    value = whole_job_rate(args.steps, world, total_s)
     e = np.sort(np.concatenate([case.T[:, [0, 1]], case.T[:, [1, 2]], case.T[:, [2, 0]]]), axis=1)
     nnz = 2 * len(np.unique(e, axis=0))          # off-diagonal entries of the node graph
     per_iter = algorithmic_bytes_per_iteration(case.n_nodes, case.n_tris, nnz, args.mode, cg_mean)
     it_ms = statistics.mean(iter_ms)
     achieved = per_iter * n_iter / (it_ms / 1e3) / 1e9
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        with open(pk_path) as fh:
-            peaks = json.load(fh)
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak, peak_src = peak_hbm()
     line = {
         "metric": "registrations/s", "value": value, "unit": "registrations/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -316,7 +362,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": "k_iterate (persistent: sample + force + solve, all iterations)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                     "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": per_iter * n_iter,
                      "traffic": None},
         "clocks": clk,
@@ -334,6 +380,169 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     reg.close()
 
+# ---------------------------------------------------------- batched form
+BATCH_LAUNCHES = 9   # prefilter rows + columns, Re at nodes, pixel fill + map,
+                     # persistent iteration kernel, energy sums, warp, MSD sums
+
+
+def batch_workload_config(args, cases, shape=None):
+    sides = [c.spec.side for c in cases]
+    nodes = [c.n_nodes for c in cases]
+    n_iter = cases[0].spec.n_iter
+    cfg = {"workload": f"config3: batch of {len(cases)} pairs, sides {min(sides)}-{max(sides)} px "
+                       f"(log-uniform), {min(nodes)}-{max(nodes)} nodes ({sum(nodes)} total), "
+                       f"{n_iter} iterations each, {args.mode} {MODE_NAMES[args.mode]}, {args.grad}",
+           "pairs": len(cases), "pixels": int(sum(s * s for s in sides)), "nodes": int(sum(nodes)),
+           "triangles": int(sum(c.n_tris for c in cases)), "iterations": n_iter,
+           "mode": args.mode, "grad": args.grad, "coeff": args.coeff,
+           "alpha": cases[0].spec.alpha, "tau": cases[0].spec.tau,
+           "l2": "flushed between timed steps (256 MiB write); the packed batch (~1.3 GB) exceeds L2",
+           "parallelism": f"replicas x{args.gpus} (the whole batch per GPU per step)"}
+    if shape is not None:
+        cfg["team"] = {"ctas": shape[0], "block": shape[1], "teams": shape[2]}
+    return cfg
+
+
+def batch_cases():
+    return inputs.make_cases(inputs.batched_specs(3))
+
+
+def oracle_batch_time(cases, mode: str, grad: str, n_sample_pairs: int = 8, sample_iters: int = 10):
+    """Seconds for the FP64 oracle to register the whole batch, estimated from
+    n_sample_pairs pairs spread over the size range (set-up, sample_iters of
+    the iterations scaled to the full count, MSD), scaled by total nodes."""
+    order = np.argsort([c.n_nodes for c in cases])
+    pick = [int(order[round(k * (len(order) - 1) / (n_sample_pairs - 1))])
+            for k in range(n_sample_pairs)]
+    t_pick = sum(oracle_registration_time(cases[k], mode, grad, sample_iters)[0] for k in pick)
+    scale = sum(c.n_nodes for c in cases) / sum(cases[k].n_nodes for k in pick)
+    return t_pick * scale, pick, sample_iters
+
+
+def run_ours_batch(args, rank, world, local_rank):
+    import torch
+    from paper_1411_2141_gb300 import mreg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    mreg.load()
+    cases = batch_cases()
+    n_iter = cases[0].spec.n_iter
+    stream = torch.cuda.current_stream()
+    bf16 = args.coeff == "bf16"
+    pairs = [(c.V, c.T, c.Re, c.Te) for c in cases]
+    b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode, grad=args.grad,
+                   coeff_bf16=bf16, stream=stream)
+    t0 = time.perf_counter()
+    ctas, block, tune_ms = b.tune(n_iter, stream)
+    tune_s = time.perf_counter() - t0
+    shape = b.shape()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        b.run(n_iter, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iter_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        b.run(n_iter, stream)
+        ends[k].record(stream)
+        iter_ms.append(b.iterate_ms())   # waits for this step's kernel only
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    msd = b.msd(stream)
+    cg = []
+    nnz_total, per_iter_total = 0, 0.0
+    for k, c in enumerate(cases):
+        its = b.get_field(k, mreg.MREG_FIELD_PCG_ITERS)
+        cgm = float(its.mean()) if args.mode != "S0" and len(its) else 0.0
+        cg.append(cgm)
+        e = np.sort(np.concatenate([c.T[:, [0, 1]], c.T[:, [1, 2]], c.T[:, [2, 0]]]), axis=1)
+        nnz = 2 * len(np.unique(e, axis=0))
+        nnz_total += nnz
+        per_iter_total += algorithmic_bytes_per_iteration(c.n_nodes, c.n_tris, nnz, args.mode, cgm)
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = [(c.V, c.T, torch.from_numpy(c.Re).pin_memory().numpy(),
+                   torch.from_numpy(c.Te).pin_memory().numpy()) for c in cases]
+        e2e_steps = max(2, min(args.steps, 3))
+
+        def e2e_once():
+            with mreg.Batch(pinned, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
+                            grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
+                            stream=stream) as bb:
+                bb.run(n_iter, stream)
+                m = bb.msd(stream)
+                us = [bb.get_u(k, stream) for k in range(len(cases))]
+            return m, us
+        e2e_once()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_once()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        h2d = sum(c.Re.nbytes + c.Te.nbytes + c.V.nbytes + c.T.nbytes for c in cases)
+        d2h = 8 * len(cases) + sum(c.V.nbytes for c in cases)
+        e2e = {"value": whole_job_rate(e2e_steps * len(cases), world, e2e_s),
+               "unit": "registrations/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+               "note": "each step creates the batch from pinned host arrays (host topology "
+                       "build of every mesh included), runs it, reads MSD and u, destroys it"}
+    if rank != 0:
+        b.close()
+        return
+    value = whole_job_rate(args.steps * len(cases), world, total_s)
+    it_ms = statistics.mean(iter_ms)
+    achieved = per_iter_total * n_iter / (it_ms / 1e3) / 1e9
+    peak, peak_src = peak_hbm()
+    before = np.array([np.mean((c.Re.astype(np.float64) - c.Te) ** 2) for c in cases])
+    line = {
+        "metric": "registrations/s", "value": value, "unit": "registrations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": batch_workload_config(args, cases, shape),
+        "node_iters_per_s": value / len(cases) * sum(c.n_nodes for c in cases) * n_iter,
+        "msd_mean": float(msd.mean()), "msd_ratio_mean": float((msd / before).mean()),
+        "cg_iters_mean": float(np.mean(cg)),
+        "iteration_kernel_ms": it_ms,
+        "autotune": {"seconds": tune_s, "chosen": [ctas, block],
+                     "ms": {f"{c}x{k}": v for (c, k), v in tune_ms.items()}},
+        "roofline": {"kernel": "k_batch (persistent: every pair's sample + force + solve loop)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": per_iter_total * n_iter, "traffic": None},
+        "clocks": clk,
+        "gpu_launches": BATCH_LAUNCHES * args.steps,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        t_all, pick, si = oracle_batch_time(cases, args.mode, args.grad)
+        line["cpu_baseline"] = {
+            "value": len(cases) / t_all, "unit": "registrations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(pick)} of {len(cases)} pairs spread over the size range: set-up + "
+                      f"{si} of {n_iter} iterations (scaled x{n_iter / si:g}) + MSD each, "
+                      f"scaled to the batch by node count; numpy/scipy FP64, 1 thread"}
+    print(json.dumps(line), flush=True)
+    b.close()
+
 
 def main():
     args = parse()
@@ -348,7 +557,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.config == 3:
+            run_ours_batch(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

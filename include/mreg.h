@@ -141,6 +141,11 @@ typedef struct {
                           precision.  Halves the coefficient footprint; the
                           error this adds is stated against the FP64 method,
                           not bounded by the FP32 tolerances.  (default 0)  */
+  int32_t team_ctas;   /* batched engine only: CTAs per team (one thread-block
+                          cluster registers one pair at a time): 1, 2, 4 or
+                          8; 0 = 2.  block_size is the team CTAs' size there
+                          and grid_blocks the number of teams (0 = as many
+                          as are co-resident, at most one per pair).        */
 } mreg_options;
 
 typedef struct {
@@ -277,6 +282,72 @@ void mreg_destroy(mreg_handle* h);
  * threads) race on it and must be serialised by the caller.              */
 mreg_status mreg_prefilter_noalloc(const float* img_dev, int64_t row_stride, float* coef_dev,
                                    int32_t width, int32_t height, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched engine: many registration problems of uneven size (images and
+ * meshes), registered together on one GPU.  The paper registers one pair at
+ * a time; the batch runs the same steps (a0-a4, Algorithm 1) for every pair
+ * with the shared options, alpha and tau.
+ *
+ * Layout: every per-pixel, per-node, per-triangle and per-edge array of all
+ * pairs is packed into one device arena.  A run is one launch sequence: the
+ * set-up steps over all pairs (one kernel each), ONE persistent kernel whose
+ * teams (thread-block clusters of team_ctas CTAs) take pairs from a queue,
+ * largest first, and run the whole iteration loop of a pair before taking
+ * the next, then the energy sums and the warp + MSD over all pairs.  The
+ * sequence is recorded once into a CUDA graph per (n_iters, team shape) and
+ * replayed.  A pair's results depend on the team shape (the order of its
+ * reductions) but not on the other pairs or on which team ran it.
+ * ------------------------------------------------------------------------ */
+typedef struct mreg_batch mreg_batch;
+
+/* Validate and copy n_pairs problems (meshes[i], Re[i], Te[i]; each as in
+ * mreg_create, images on the host or the device) and build their set-up.
+ * opts: as for mreg_create (engine is ignored) plus team_ctas; block_size 0
+ * means 256 threads.  The call returns after the set-up work on stream has
+ * finished.  Errors: as mreg_create, for the first failing pair (the message
+ * names it); INVALID_ARG for n_pairs < 1 or NULL arrays.                    */
+mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mreg_image* Re,
+                              const mreg_image* Te, double alpha, double tau,
+                              const mreg_options* opts, void* stream, mreg_batch** out);
+
+/* Register every pair from u = 0: prefilter, node samples and pixel map,
+ * n_iters iterations (n_iters >= 1), warp and MSD.  Asynchronous (a CUDA
+ * graph launch on stream; the first call for a given n_iters and team shape
+ * also records the graph).                                                  */
+mreg_status mreg_batch_run(mreg_batch* b, int32_t n_iters, void* stream);
+
+/* Autotuner: times mreg_batch_run(n_iters) for every supported team shape
+ * (team_ctas in 1, 2, 4, 8 x block_size in 128, 256, 512, skipping shapes
+ * that do not fit), keeps the fastest for later runs and returns it.  Each
+ * shape is run once to warm up and timed on the best of two runs with CUDA
+ * events.  times_ms (may be NULL) receives 12 entries, row-major over
+ * (team_ctas, block_size), -1 for skipped shapes.  Blocks.                  */
+mreg_status mreg_batch_tune(mreg_batch* b, int32_t n_iters, void* stream, int32_t* team_ctas,
+                            int32_t* block_size, float* times_ms);
+
+/* Current team shape and number of teams. */
+mreg_status mreg_batch_shape(mreg_batch* b, int32_t* team_ctas, int32_t* block_size,
+                             int32_t* n_teams);
+
+/* Device time of the persistent iteration kernel (with its energy sums) in
+ * the last run, in ms, from CUDA events recorded around it inside the run.
+ * Blocks until that run has finished.                                      */
+mreg_status mreg_batch_iterate_ms(mreg_batch* b, float* ms);
+
+/* MSD of every pair after the last run (n_pairs doubles).  Blocks.         */
+mreg_status mreg_batch_msd(mreg_batch* b, double* out_host, void* stream);
+
+/* One MREG_FIELD_* array of one pair (as mreg_get_field; FORCE is the force
+ * of the run's last iteration).                                             */
+mreg_status mreg_batch_get_field(mreg_batch* b, int32_t pair, int32_t field, void* dst,
+                                 int32_t dst_on_device, int64_t* count_out, void* stream);
+
+/* Solver state of one pair after the last run (as mreg_stats). Blocks.     */
+mreg_status mreg_batch_stats(mreg_batch* b, int32_t pair, mreg_stats_t* out, void* stream);
+
+/* Release everything (after the batch's work finished).  NULL is accepted. */
+void mreg_batch_destroy(mreg_batch* b);
 
 /* Message of the last error on this thread ("" if none). */
 const char* mreg_last_error(void);

@@ -19,8 +19,8 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libmreg.so")
 
-SOURCES = ["api.cpp", "prefilter.cu", "iterate.cu", "iterate_cluster.cu", "warp.cu",
-           "prefilter_noalloc.cu"]
+SOURCES = ["api.cpp", "batch_api.cpp", "prefilter.cu", "iterate.cu", "iterate_cluster.cu",
+           "batch.cu", "warp.cu", "prefilter_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -15,11 +15,15 @@
 #include <string>
 #include <vector>
 
+#include "host_common.h"
 #include "mreg_internal.h"
 
-namespace {
+namespace mreg {
+namespace host {
 
+namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
 mreg_status fail(mreg_status st, const char* fmt, ...) {
   char buf[512];
@@ -36,33 +40,9 @@ mreg_status cuda_fail(cudaError_t e, const char* what) {
   return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                  \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
-  } while (0)
 
-constexpr int kHistCap = 4096;
-constexpr int kChunk = 1024;   // iterations per launch of the iteration kernel
-constexpr int kMaxPcgIt = 10000;
-constexpr double kDegenerateRel = 1e-12;
 
-// Host-side mesh data and operators, built once per mesh.
-struct HostMesh {
-  int nV = 0, nT = 0, nE = 0, nnz = 0;
-  std::vector<float> xy;
-  std::vector<int> tri;                   // counter-clockwise
-  std::vector<int> inc_ptr, inc_tri;      // incident triangles, ascending
-  std::vector<int> inc_opp;               // 2 per incidence: the other corners, CCW
-  std::vector<int> adj_ptr, adj_col, adj_edge;
-  std::vector<int> edges;                 // 2 per edge, a < b
-  std::vector<float> edge_w;              // sum over the edge's triangles of A_T / 3
-  std::vector<float> lumped;              // A(V_a) / 3
-  std::vector<float> Mdiag, Moff, Adiag, Aoff, dinv;
-  double area_floor = 0.0;
-};
-
-int find_in_row(const HostMesh& m, int i, int j) {
+static int find_in_row(const HostMesh& m, int i, int j) {
   const int* b = m.adj_col.data() + m.adj_ptr[i];
   const int* e = m.adj_col.data() + m.adj_ptr[i + 1];
   const int* p = std::lower_bound(b, e, j);
@@ -231,7 +211,17 @@ mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam
   return MREG_OK;
 }
 
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace host
+}  // namespace mreg
+
+using namespace mreg::host;   // NOLINT
+
+#define CK MREG_CK
+
+namespace {
+
+constexpr int kHistCap = 4096;
+constexpr int kChunk = 1024;   // iterations per launch of the iteration kernel
 
 }  // namespace
 
@@ -337,7 +327,8 @@ struct mreg_handle {
   }
 };
 
-namespace {
+namespace mreg {
+namespace host {
 
 mreg_status validate_image(const mreg_image* im, const char* name) {
   if (!im) return fail(MREG_ERR_INVALID_ARG, "%s is NULL", name);
@@ -361,6 +352,33 @@ mreg_status validate_image(const mreg_image* im, const char* name) {
   }
   return MREG_OK;
 }
+
+mreg_status validate_options(const mreg_options& o, double alpha, double tau, double* lam) {
+  if (o.mode < 0 || o.mode > 2) return fail(MREG_ERR_INVALID_ARG, "unknown mode %d", o.mode);
+  if (o.grad < 0 || o.grad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown grad %d", o.grad);
+  if (o.quad < 0 || o.quad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown quad %d", o.quad);
+  if (o.quad == MREG_QUAD_EDGE_MIDPOINTS &&
+      (o.mode != MREG_MODE_FEM_IMPLICIT || o.grad != MREG_GRAD_SPLINE))
+    return fail(MREG_ERR_INVALID_ARG, "edge-midpoint quadrature needs the FEM mode and the spline gradient");
+  if (!(o.pcg_rtol > 0.0) || !(o.pcg_rtol < 1.0)) return fail(MREG_ERR_INVALID_ARG, "pcg_rtol must be in (0,1)");
+  if (o.pcg_maxit < 1 || o.pcg_maxit > kMaxPcgIt)
+    return fail(MREG_ERR_INVALID_ARG, "pcg_maxit must be in [1, %d]", kMaxPcgIt);
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 512 || o.block_size % 32))
+    return fail(MREG_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
+  if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
+  if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
+  if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
+    return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
+  const double l = o.lambda < 0.0 ? tau * alpha : o.lambda;
+  if (!std::isfinite(l)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
+  *lam = l;
+  return MREG_OK;
+}
+
+}  // namespace host
+}  // namespace mreg
+
+namespace {
 
 // Copy an image into a dense device buffer (device images are checked for
 // finiteness on the device first).
@@ -455,24 +473,9 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   mreg_options o;
   mreg_default_options(&o);
   if (opts) o = *opts;
-  if (o.mode < 0 || o.mode > 2) return fail(MREG_ERR_INVALID_ARG, "unknown mode %d", o.mode);
-  if (o.grad < 0 || o.grad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown grad %d", o.grad);
-  if (o.quad < 0 || o.quad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown quad %d", o.quad);
-  if (o.quad == MREG_QUAD_EDGE_MIDPOINTS &&
-      (o.mode != MREG_MODE_FEM_IMPLICIT || o.grad != MREG_GRAD_SPLINE))
-    return fail(MREG_ERR_INVALID_ARG, "edge-midpoint quadrature needs the FEM mode and the spline gradient");
-  if (!(o.pcg_rtol > 0.0) || !(o.pcg_rtol < 1.0)) return fail(MREG_ERR_INVALID_ARG, "pcg_rtol must be in (0,1)");
-  if (o.pcg_maxit < 1 || o.pcg_maxit > kMaxPcgIt)
-    return fail(MREG_ERR_INVALID_ARG, "pcg_maxit must be in [1, %d]", kMaxPcgIt);
-  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 512 || o.block_size % 32))
-    return fail(MREG_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
-  if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
-  if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
-  if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
-    return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
-  const double lam = o.lambda < 0.0 ? tau * alpha : o.lambda;
-  if (!std::isfinite(lam)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
-
+  double lam = 0.0;
+  st = validate_options(o, alpha, tau, &lam);
+  if (st) return st;
   const int W = Re->width, H = Re->height;
   HostMesh hm;
   try {

@@ -1,0 +1,55 @@
+// Host-side pieces shared by the C ABI entry points of the one-pair handle
+// (api.cpp) and of the batched engine (batch_api.cpp): error reporting, image
+// validation and the mesh topology builder (Algorithm 1, "Pre-Computation":
+// 1-ring, neighbour triangles, operator matrices).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "mreg.h"
+
+namespace mreg {
+namespace host {
+
+constexpr int kMaxPcgIt = 10000;
+constexpr double kDegenerateRel = 1e-12;
+
+// Host-side mesh data and operators, built once per mesh.
+struct HostMesh {
+  int nV = 0, nT = 0, nE = 0, nnz = 0;
+  std::vector<float> xy;
+  std::vector<int> tri;                   // counter-clockwise
+  std::vector<int> inc_ptr, inc_tri;      // incident triangles, ascending
+  std::vector<int> inc_opp;               // 2 per incidence: the other corners, CCW
+  std::vector<int> adj_ptr, adj_col, adj_edge;
+  std::vector<int> edges;                 // 2 per edge, a < b
+  std::vector<float> edge_w;              // sum over the edge's triangles of A_T / 3
+  std::vector<float> lumped;              // A(V_a) / 3
+  std::vector<float> Mdiag, Moff, Adiag, Aoff, dinv;
+  double area_floor = 0.0;
+};
+
+// Record the message returned by mreg_last_error(); returns st.
+mreg_status fail(mreg_status st, const char* fmt, ...);
+mreg_status cuda_fail(cudaError_t e, const char* what);
+// Validates and copies the mesh and builds its topology and operators for
+// the given mode and smoothing weight.
+mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m);
+// Size, stride and (host images) finiteness checks.
+mreg_status validate_image(const mreg_image* im, const char* name);
+// Option checks shared by every entry point that takes mreg_options;
+// *lam receives the smoothing weight.
+mreg_status validate_options(const mreg_options& o, double alpha, double tau, double* lam);
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace host
+}  // namespace mreg
+
+#define MREG_CK(call, what)                                       \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return ::mreg::host::cuda_fail(e_, what); \
+  } while (0)

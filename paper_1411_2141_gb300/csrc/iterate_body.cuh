@@ -1,0 +1,698 @@
+// The loop body of Algorithm 1 (steps a1-a3), written once for a "team" of
+// thread blocks that runs one registration: the whole cooperative grid
+// (iterate.cu, one pair per launch) or one thread-block cluster (batch.cu,
+// many pairs per launch).  A team provides
+//   int rank, nb;   // this block's index in the team, blocks in the team
+//   bool sync();    // barrier over the team with release/acquire ordering;
+//                   // false: the run was aborted and the body must return
+// and the body keeps every decision team-uniform: control flow follows only
+// the totals of fixed-order reductions, which all blocks compute alike.
+//
+// Phases:
+//   sample   (a1, Eq. 2-4)  f_i = Te(V_i + u_i) by the cubic B-spline,
+//            r_i = f_i - Re(V_i), data energy 1/2 sum w_i r_i^2.  With the
+//            spline gradient the force F_i = w_i r_i grad Te is formed here.
+//            Edge form: the same at the edge midpoints, h_e = 1/2 w_e r_e grad Te.
+//   force    (a2, Eq. 6, 9, 10)  mesh gradient of f on the deformed mesh,
+//            node-centric over the ascending incident-triangle list (no
+//            atomics); F_i = w_i r_i g_i.  Edge form: F_a = sum of h_e over the
+//            edges at a.
+//   explicit (a3, S0: Eq. 5, 14)  u_i <- (1-l) u0_i + l mean_{j in N1(i)} u0_j,
+//            u0 = u - tau F; the next iteration's sample is taken right away
+//            at the new u_i.  Two barriers per iteration (one with the spline
+//            gradient).
+//   implicit (a3, S1/S2)  b = D_m (u - tau F) or M u - tau F in float-float;
+//            A u' = b by Jacobi-preconditioned conjugate gradients from the
+//            warm start u, x and y sharing every matrix pass.  The CG is the
+//            single-reduction form of Chronopoulos and Gear (J. Comput. Appl.
+//            Math. 25, 1989): each CG iteration is ONE team phase.  Its node
+//            update needs the neighbours' next z' = D^-1 (r - a s') (and, to
+//            check convergence, the next iterate x' = x + a p'); every node
+//            recomputes those from the neighbours' current state with the
+//            same expressions the owners use, so the values agree bitwise and
+//            no extra barrier is needed.  Once the recursive residual is
+//            within 100x of the target, each step also forms the true
+//            residual b - A x' in float-float and samples Te at x' for the
+//            next iteration; the solve ends when the true residual passes
+//            rtol * ||b|| for both components.  If the FP32 recursion drifts
+//            10x below the true residual, CG restarts from it (iterative
+//            refinement); a cap on CG iterations ends a solve that cannot
+//            converge and is reported.
+//
+// Data that change during the loop (u, the CG state, f, F) are read with
+// plain loads; __ldg is used only for data written before the launch.
+//
+// Latency: a phase costs a team barrier, a reduction, and a few dependent L2
+// round trips (~290 cycles each), so each phase is shaped to have as few
+// dependent global loads as possible.  The static topology of each thread's
+// first node (neighbours, their Jacobi entries, incident-triangle corner
+// pairs, row bounds) is cached in shared memory and registers at the start,
+// and neighbour data are gathered in unrolled groups so their loads are in
+// flight together.
+//
+// The Eq. 9 triangle gradient is evaluated in the algebraically identical
+// edge-normal form A_T grad f_T = sign(A) / 2 * (df1 * rot(e2) - df2 * rot(e1))
+// with e1, e2 the edge vectors from the node and df the value differences;
+// this avoids the 1/(4A^2) scaling and the cancellation of the dot-product
+// form.  Deformed edge vectors are (V_j - V_i) + (u_j - u_i).
+#pragma once
+
+#include "iterate_common.cuh"
+
+namespace mreg {
+namespace {
+
+constexpr int kIterBlockMax = 512;
+constexpr int kCacheA = 10;   // adjacency entries cached per thread
+constexpr int kCacheI = 10;   // incidence entries cached per thread
+constexpr float kVerifyGate = 1.0e4f;   // verify once ||r||^2 <= 1e4 rtol^2 ||b||^2
+
+size_t topo_smem_bytes(int block) {
+  return (size_t)block * (kCacheA * (sizeof(int) + sizeof(float)) + kCacheI * sizeof(int2));
+}
+
+// Readers of f for the mesh gradient.
+struct FPlain {
+  const float* f;
+  __device__ __forceinline__ float operator()(int j) const { return f[j]; }
+};
+
+// Static topology of the thread's first node, cached in shared memory (SoA
+// by thread, conflict-free); later nodes of the thread read global memory.
+struct Topo {
+  int* sadj;     // [kCacheA][bd] neighbours
+  float* sdj;    // [kCacheA][bd] their Jacobi entries 1/diag(A)
+  int2* sinc;    // [kCacheI][bd] incident-triangle corner pairs
+  int bd, t;
+  int abeg, adeg, ibeg, ideg;   // row bounds of the first node (registers)
+
+  __device__ __forceinline__ void fill(const IterArgs& a, int i) {
+    const int ab = __ldg(a.adj_ptr + i), ad = __ldg(a.adj_ptr + i + 1) - ab;
+    abeg = ab;
+    adeg = ad;
+    ibeg = __ldg(a.inc_ptr + i);
+    ideg = __ldg(a.inc_ptr + i + 1) - ibeg;
+    for (int k = 0; k < ad && k < kCacheA; ++k) {
+      const int j = __ldg(a.adj_col + ab + k);
+      sadj[k * bd + t] = j;
+      sdj[k * bd + t] = __ldg(a.dinv + j);
+    }
+    for (int k = 0; k < ideg && k < kCacheI; ++k) sinc[k * bd + t] = __ldg(a.inc_opp + ibeg + k);
+  }
+  // adjacency / incidence row of node i: registers for the first node
+  __device__ __forceinline__ void arow(const IterArgs& a, bool cached, int i, int& beg, int& deg) const {
+    if (cached) {
+      beg = abeg;
+      deg = adeg;
+    } else {
+      beg = __ldg(a.adj_ptr + i);
+      deg = __ldg(a.adj_ptr + i + 1) - beg;
+    }
+  }
+  __device__ __forceinline__ void irow(const IterArgs& a, bool cached, int i, int& beg, int& deg) const {
+    if (cached) {
+      beg = ibeg;
+      deg = ideg;
+    } else {
+      beg = __ldg(a.inc_ptr + i);
+      deg = __ldg(a.inc_ptr + i + 1) - beg;
+    }
+  }
+  __device__ __forceinline__ int adj(const IterArgs& a, bool cached, int beg, int k) const {
+    return (cached && k < kCacheA) ? sadj[k * bd + t] : __ldg(a.adj_col + beg + k);
+  }
+  __device__ __forceinline__ float dj(const IterArgs& a, bool cached, int j, int k) const {
+    return (cached && k < kCacheA) ? sdj[k * bd + t] : __ldg(a.dinv + j);
+  }
+  __device__ __forceinline__ int2 inc(const IterArgs& a, bool cached, int beg, int k) const {
+    return (cached && k < kCacheI) ? sinc[k * bd + t] : __ldg(a.inc_opp + beg + k);
+  }
+};
+
+// Eq. 10 with Eq. 9 (see mesh_gradient in iterate_common.cuh), gathering the
+// incident triangles two at a time.
+template <class DISP, class FVAL>
+__device__ __forceinline__ float2 mesh_gradient_c(const IterArgs& a, const Topo& T, bool cached,
+                                                  const DISP& disp, const FVAL& fval, int i,
+                                                  float2 Vi, float2 ui, float fi) {
+  float nx = 0.0f, ny = 0.0f, den = 0.0f;
+  int beg, deg;
+  T.irow(a, cached, i, beg, deg);
+  for (int k0 = 0; k0 < deg; k0 += 2) {
+    int2 jk[2];
+    float2 Vj[2], Vk[2], uj[2], uk[2];
+    float fj[2], fk[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) jk[u] = (k0 + u < deg) ? T.inc(a, cached, beg, k0 + u) : make_int2(i, i);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      Vj[u] = __ldg(a.V + jk[u].x);
+      Vk[u] = __ldg(a.V + jk[u].y);
+      uj[u] = disp(jk[u].x);
+      uk[u] = disp(jk[u].y);
+      fj[u] = fval(jk[u].x);
+      fk[u] = fval(jk[u].y);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (k0 + u >= deg) continue;
+      const float e1x = (Vj[u].x - Vi.x) + (uj[u].x - ui.x), e1y = (Vj[u].y - Vi.y) + (uj[u].y - ui.y);
+      const float e2x = (Vk[u].x - Vi.x) + (uk[u].x - ui.x), e2y = (Vk[u].y - Vi.y) + (uk[u].y - ui.y);
+      const float A2 = e1x * e2y - e1y * e2x;          // twice the signed area
+      const float area = 0.5f * fabsf(A2);
+      if (!(area > a.area_floor)) continue;             // degenerate: weight 0
+      const float df1 = fj[u] - fi, df2 = fk[u] - fi;
+      const float h = A2 > 0.0f ? 0.5f : -0.5f;
+      nx += h * (df1 * e2y - df2 * e1y);
+      ny += h * (df2 * e1x - df1 * e2x);
+      den += area;
+    }
+  }
+  if (den > 0.0f) return make_float2(nx / den, ny / den);
+  return make_float2(0.0f, 0.0f);
+}
+
+template <int FORM, class DISP, class FVAL>
+__device__ __forceinline__ float2 neighbour_force_c(const IterArgs& a, const Topo& T, bool cached,
+                                                    const DISP& disp, const FVAL& fval, int i,
+                                                    float2 ui, float fi) {
+  if (FORM == kFormFemEdges) return neighbour_force<FORM>(a, disp, fval, i, ui, fi);
+  const float2 Vi = __ldg(a.V + i);
+  const float2 g = mesh_gradient_c(a, T, cached, disp, fval, i, Vi, ui, fi);
+  const float r = fi - __ldg(a.ReV + i);
+  const float wr = (FORM == kFormFemNodes) ? __ldg(a.lumped + i) * r : r;
+  return make_float2(wr * g.x, wr * g.y);
+}
+
+#define MY_REC (a.part + ((size_t)par * nb + team.rank) * kRec)
+#define ALL_REC (a.part + (size_t)par * nb * kRec)
+#define SYNC_OR_LEAVE()             \
+  do {                              \
+    if (!team.sync()) return false; \
+  } while (0)
+// node loop: thread-strided; the first node of each thread has cached topology
+#define FOR_NODES(i, cached) \
+  for (int i = tid, slot_ = 0; i < nV; i += nth, ++slot_) if (const bool cached = slot_ == 0; true)
+
+// ======================================================================
+// S0: explicit step and one umbrella smoothing pass (Algorithm 1 exactly)
+// ======================================================================
+template <int GRAD, class TEAM>
+__device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsigned char* dsm) {
+  const int tid = team.rank * blockDim.x + threadIdx.x;
+  const int nth = team.nb * blockDim.x;
+  const int nV = a.nV;
+  const int bd = blockDim.x;
+  const int gwarp = tid >> 5;   // energy partials are kept per warp
+  Topo T{(int*)dsm, (float*)(dsm + (size_t)kCacheA * bd * sizeof(int)),
+         (int2*)(dsm + (size_t)kCacheA * bd * (sizeof(int) + sizeof(float))), bd, (int)threadIdx.x};
+  if (tid < nV) T.fill(a, tid);
+  const DispPlain disp{a.u};
+  const FPlain fval{a.f};
+
+  {  // sample at the initial u
+    ff e = ff_zero();
+    for (int i = tid; i < nV; i += nth) {
+      const float2 ui = a.u[i];
+      float2 Fi;
+      e = ff_add_f(e, sample_node<kFormExplicit, GRAD>(a, i, ui, a.f + i, a.F + i, &Fi));
+      if (GRAD == 1) a.u0[i] = make_float2(ui.x - a.tau * Fi.x, ui.y - a.tau * Fi.y);
+    }
+    warp_energy_store(e, a.epart, gwarp);   // energy of iteration 0
+    SYNC_OR_LEAVE();
+  }
+  for (int it = 0; it < a.n_iters; ++it) {
+    // Double buffers by iteration parity: u - tau F and F, so that the sample
+    // of iteration it+1 may be written while slow blocks still read those of
+    // iteration it.
+    float2* u0 = a.u0 + (size_t)(it & 1) * nV;
+    float2* u0n = a.u0 + (size_t)((it + 1) & 1) * nV;
+    float2* F = a.F + (size_t)(it & 1) * nV;
+    float2* Fn = a.F + (size_t)((it + 1) & 1) * nV;
+    if (GRAD == 0) {   // force (Eq. 6, 9, 10) and the step (Eq. 5)
+      FOR_NODES(i, cached) {
+        const float2 ui = a.u[i];
+        const float2 Fi = neighbour_force_c<kFormExplicit>(a, T, cached, disp, fval, i, ui, a.f[i]);
+        F[i] = Fi;
+        u0[i] = make_float2(ui.x - a.tau * Fi.x, ui.y - a.tau * Fi.y);
+      }
+      SYNC_OR_LEAVE();   // u0 of every node is needed below
+    }
+    // one umbrella smoothing pass (Eq. 14), then the next sample
+    ff e = ff_zero();
+    const float lam = a.lam;
+    FOR_NODES(i, cached) {
+      int beg, deg;
+      T.arow(a, cached, i, beg, deg);
+      float sx = 0.0f, sy = 0.0f;
+      for (int k0 = 0; k0 < deg; k0 += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (k0 + u < deg) ? u0[T.adj(a, cached, beg, k0 + u)] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (k0 + u < deg) {
+            sx += v[u].x;
+            sy += v[u].y;
+          }
+        }
+      }
+      const float inv_m = 1.0f / (float)deg;
+      const float2 c = u0[i];
+      const float2 un = make_float2((1.0f - lam) * c.x + lam * (sx * inv_m),
+                                    (1.0f - lam) * c.y + lam * (sy * inv_m));
+      a.u[i] = un;
+      float2 Fv;
+      e = ff_add_f(e, sample_node<kFormExplicit, GRAD>(a, i, un, a.f + i, Fn + i, &Fv));
+      if (GRAD == 1) u0n[i] = make_float2(un.x - a.tau * Fv.x, un.y - a.tau * Fv.y);
+    }
+    warp_energy_store(e, a.epart + (size_t)(it + 1) * a.ewarps, gwarp);
+    SYNC_OR_LEAVE();
+  }
+  return true;
+}
+
+// ======================================================================
+// S1 / S2: semi-implicit step, single-reduction Jacobi-PCG
+// ======================================================================
+
+// Solve set-up for node i: b, r0 = b - A x0 (float-float) and z0 = D^-1 r0
+// into the CG state (x is rewritten with its own value); adds ||b||^2,
+// ||r0||^2 and r0.z0 (x, y) to acc[0..6).
+template <int FORM>
+__device__ __forceinline__ void init_node_c(const IterArgs& a, const Topo& T, bool cached,
+                                            const DispCg& disp, float4* st, int i, float2 xi,
+                                            float2 Fi, float* acc) {
+  int beg, deg;
+      T.arow(a, cached, i, beg, deg);
+  const ff tau = ff_load(a.tau_ff);
+  ff bx, by;
+  AxAcc<FORM> A;
+  A.init(a, i, xi);
+  if (FORM == kFormUmbrella) {
+    bx = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.x)), xi.x), (float)deg);   // D_m (u - tau F)
+    by = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.y)), xi.y), (float)deg);
+  } else {
+    const float md = __ldg(a.Mdiag + i);   // M u - tau F
+    bx = ff_prod(md, xi.x);
+    by = ff_prod(md, xi.y);
+  }
+  for (int k0 = 0; k0 < deg; k0 += 4) {
+    float2 xj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xj[u] = (k0 + u < deg) ? disp(T.adj(a, cached, beg, k0 + u)) : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u >= deg) continue;
+      A.add(a, beg + k0 + u, xj[u]);
+      if (FORM != kFormUmbrella) {
+        const float mo = __ldg(a.Moff + beg + k0 + u);
+        bx = ff_add(bx, ff_prod(mo, xj[u].x));
+        by = ff_add(by, ff_prod(mo, xj[u].y));
+      }
+    }
+  }
+  if (FORM != kFormUmbrella) {
+    bx = ff_add(bx, ff_neg(ff_mul_f(tau, Fi.x)));
+    by = ff_add(by, ff_neg(ff_mul_f(tau, Fi.y)));
+  }
+  A.finish(a, deg, xi);
+  a.b[i] = make_float4(bx.hi, bx.lo, by.hi, by.lo);
+  const float2 r = make_float2(ff_to_f(ff_add(bx, ff_neg(A.ax))), ff_to_f(ff_add(by, ff_neg(A.ay))));
+  const float di = __ldg(a.dinv + i);
+  const float2 z = make_float2(__fmul_rn(di, r.x), __fmul_rn(di, r.y));
+  float4* node = st + 3 * (size_t)i;
+  node[0] = make_float4(xi.x, xi.y, z.x, z.y);
+  node[1] = make_float4(0.0f, 0.0f, r.x, r.y);   // p is set by the first step
+  const float bxf = ff_to_f(bx), byf = ff_to_f(by);
+  acc[0] += bxf * bxf;
+  acc[1] += byf * byf;
+  acc[2] += r.x * r.x;
+  acc[3] += r.y * r.y;
+  acc[4] += r.x * z.x;
+  acc[5] += r.y * z.y;
+}
+
+// One CG step for node i (state st -> st_out).  VERIFY: also the true
+// residual of x' (float-float, into a.rt and c[4..6)) and the sample at x'.
+// Adds gamma' = r'.z' (x, y), delta' = w'.z' and ||r'||^2 to c[0..4), c[6..8).
+template <int FORM, int GRAD, bool VERIFY>
+__device__ __forceinline__ void cg_step_node(const IterArgs& a, const Topo& T, bool cached,
+                                             const float4* st, float4* st_out, int i,
+                                             const CgStep& step, float* c, ff& e, float2* Fn) {
+  int beg, deg;
+      T.arow(a, cached, i, beg, deg);
+  const Cg ci = load_cg(st, i);
+  const CgNext ni = cg_next(ci, __ldg(a.dinv + i), step);
+  const float ad = a_diag<FORM>(a, i, deg);
+  float wx = ad * ni.z.x, wy = ad * ni.z.y;
+  AxAcc<FORM> A;
+  if (VERIFY) A.init(a, i, ni.x);
+  constexpr int G = VERIFY ? 2 : 4;   // neighbours gathered together
+  for (int k0 = 0; k0 < deg; k0 += G) {
+    int jj[G];
+    float dd[G];
+    float4 s1[G], s2[G], s0[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const bool ok = k0 + u < deg;
+      jj[u] = ok ? T.adj(a, cached, beg, k0 + u) : i;
+      dd[u] = ok ? T.dj(a, cached, jj[u], k0 + u) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      s1[u] = st[3 * (size_t)jj[u] + 1];   // {p, r}
+      s2[u] = st[3 * (size_t)jj[u] + 2];   // {w, s}
+      if (VERIFY) s0[u] = st[3 * (size_t)jj[u]];   // {x, z}
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      if (k0 + u >= deg) continue;
+      const CgNextZ nz = cg_next_z(make_float2(s1[u].z, s1[u].w), make_float2(s2[u].x, s2[u].y),
+                                   make_float2(s2[u].z, s2[u].w), dd[u], step);
+      const float ao = a_off<FORM>(a, beg + k0 + u);
+      wx = __fmaf_rn(ao, nz.z.x, wx);
+      wy = __fmaf_rn(ao, nz.z.y, wy);
+      if (VERIFY) {
+        const float2 xj = cg_next_x(make_float2(s0[u].x, s0[u].y), make_float2(s0[u].z, s0[u].w),
+                                    make_float2(s1[u].x, s1[u].y), step, nullptr);
+        A.add(a, beg + k0 + u, xj);
+      }
+    }
+  }
+  Cg out;
+  out.x = ni.x;
+  out.z = ni.z;
+  out.p = ni.p;
+  out.r = ni.r;
+  out.w = make_float2(wx, wy);
+  out.s = ni.s;
+  store_cg(st_out, i, out);
+  c[0] += ni.r.x * ni.z.x;
+  c[1] += ni.r.y * ni.z.y;
+  c[2] += wx * ni.z.x;
+  c[3] += wy * ni.z.y;
+  c[6] += ni.r.x * ni.r.x;
+  c[7] += ni.r.y * ni.r.y;
+  if (VERIFY) {
+    A.finish(a, deg, ni.x);
+    const float4 b4 = a.b[i];
+    const float rtx = ff_to_f(ff_add(ff{b4.x, b4.y}, ff_neg(A.ax)));
+    const float rty = ff_to_f(ff_add(ff{b4.z, b4.w}, ff_neg(A.ay)));
+    a.rt[i] = make_float2(rtx, rty);
+    c[4] += rtx * rtx;
+    c[5] += rty * rty;
+    if (FORM != kFormFemEdges) {
+      float2 unusedF;
+      e = ff_add_f(e, sample_node<FORM, GRAD>(a, i, ni.x, a.f + i, Fn + i, &unusedF));
+    }
+  }
+}
+
+template <int FORM, int GRAD, class TEAM>
+__device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsigned char* dsm) {
+  __shared__ float s_red[kMaxWarps * kRec];
+  __shared__ float s_tot[2 * kRec];   // alternates with par
+  const int tid = team.rank * blockDim.x + threadIdx.x;
+  const int nth = team.nb * blockDim.x;
+  const int nb = team.nb;
+  const bool lead = team.rank == 0 && threadIdx.x == 0;
+  const int nV = a.nV;
+  const int bd = blockDim.x;
+  const int gwarp = tid >> 5;   // energy partials are kept per warp
+  constexpr bool kEdges = FORM == kFormFemEdges;
+  // the spline-gradient node forms get F from the sample itself
+  constexpr bool kForceInSample = GRAD == 1 && !kEdges;
+  Topo T{(int*)dsm, (float*)(dsm + (size_t)kCacheA * bd * sizeof(int)),
+         (int2*)(dsm + (size_t)kCacheA * bd * (sizeof(int) + sizeof(float))), bd, (int)threadIdx.x};
+  if (tid < nV) T.fill(a, tid);
+  float4* const cg[2] = {a.cg, a.cg + (size_t)3 * nV};
+  int par = 0;   // half of the partial-sum buffer used by the next reduction
+
+  // The displacement lives in the x of the CG state of parity q.
+  int q = 0;
+  for (int i = tid; i < nV; i += nth) {
+    const float2 u = a.u[i];
+    cg[0][3 * (size_t)i] = make_float4(u.x, u.y, 0.0f, 0.0f);
+  }
+  SYNC_OR_LEAVE();   // the first phase may read neighbours' x
+  bool have_sample = false;   // f (F with the spline gradient) and energy of the current x
+
+  for (int it = 0; it < a.n_iters; ++it) {
+    float2* F = a.F + (size_t)(it & 1) * nV;
+    float2* Fn = a.F + (size_t)((it + 1) & 1) * nV;
+    const DispCg disp{cg[q]};
+    const FPlain fval{a.f};
+    float init[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    bool have_init = false;
+
+    // ---- sample at the current x (when the last solve did not provide it)
+    if (!have_sample) {
+      ff e = ff_zero();
+      if (kEdges) {
+        for (int q2 = tid; q2 < a.nE; q2 += nth) {
+          const int2 ab = __ldg(a.edges + q2);
+          e = ff_add_f(e, sample_edge(a, q2, ab, disp(ab.x), disp(ab.y)));
+        }
+      } else {
+        FOR_NODES(i, cached) {
+          const float2 xi = disp(i);
+          float2 Fi;
+          e = ff_add_f(e, sample_node<FORM, GRAD>(a, i, xi, a.f + i, F + i, &Fi));
+          if (kForceInSample) init_node_c<FORM>(a, T, cached, disp, cg[q], i, xi, Fi, init);
+        }
+      }
+      warp_energy_store(e, a.epart + (size_t)it * a.ewarps, gwarp);
+      block_record<6, false>(init, ff_zero(), MY_REC, s_red);
+      SYNC_OR_LEAVE();
+      ff unused;
+      grid_totals<6, false>(ALL_REC, nb, init, unused, s_tot + par * kRec);
+      par ^= 1;
+      have_init = kForceInSample;
+    }
+    const int hi = a.it0 + it;
+
+    // ---- force (Eq. 6, 9, 10) and the solve's right-hand side ------------
+    if (!have_init) {
+      float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      FOR_NODES(i, cached) {
+        const float2 xi = disp(i);
+        float2 Fi;
+        if (kForceInSample) {
+          Fi = F[i];   // formed with the sample
+        } else {
+          Fi = neighbour_force_c<FORM>(a, T, cached, disp, fval, i, xi, a.f[i]);
+          F[i] = Fi;
+        }
+        init_node_c<FORM>(a, T, cached, disp, cg[q], i, xi, Fi, acc);
+      }
+      block_record<6, false>(acc, ff_zero(), MY_REC, s_red);
+      SYNC_OR_LEAVE();
+      ff unused;
+      grid_totals<6, false>(ALL_REC, nb, init, unused, s_tot + par * kRec);
+      par ^= 1;
+    }
+
+    // ---- solve -------------------------------------------------------------
+    const float bn2[2] = {init[0], init[1]};
+    float rt2[2] = {init[2], init[3]};
+    float rr[2] = {init[2], init[3]};   // recursive residual (FP32 recursion)
+    float gam[2] = {init[4], init[5]};
+    const float rtol2 = a.rtol2;
+    bool conv[2] = {rt2[0] <= rtol2 * bn2[0], rt2[1] <= rtol2 * bn2[1]};
+    CgStep step;
+    step.alpha = make_float2(0.0f, 0.0f);
+    step.beta = make_float2(0.0f, 0.0f);
+    step.first = true;
+    int k = 0;
+    bool capped = false;
+    bool need_w = true;   // w = A z of the current state must be formed first
+    have_sample = false;
+    while (!(conv[0] && conv[1])) {
+      if (k >= a.maxit) {
+        capped = true;
+        break;
+      }
+      if (need_w) {
+        // w = A z (the neighbours' z from the current state), delta = w.z
+        float c2[2] = {0.0f, 0.0f};
+        FOR_NODES(i, cached) {
+          int beg, deg;
+      T.arow(a, cached, i, beg, deg);
+          const float4 xz = cg[q][3 * (size_t)i];
+          const float ad = a_diag<FORM>(a, i, deg);
+          float wx = ad * xz.z, wy = ad * xz.w;
+          for (int k0 = 0; k0 < deg; k0 += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              v[u] = cg[q][3 * (size_t)((k0 + u < deg) ? T.adj(a, cached, beg, k0 + u) : i)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (k0 + u >= deg) continue;
+              const float ao = a_off<FORM>(a, beg + k0 + u);
+              wx = __fmaf_rn(ao, v[u].z, wx);
+              wy = __fmaf_rn(ao, v[u].w, wy);
+            }
+          }
+          cg[q][3 * (size_t)i + 2] = make_float4(wx, wy, 0.0f, 0.0f);
+          c2[0] += wx * xz.z;
+          c2[1] += wy * xz.w;
+        }
+        block_record<2, false>(c2, ff_zero(), MY_REC, s_red);
+        SYNC_OR_LEAVE();
+        ff unused;
+        grid_totals<2, false>(ALL_REC, nb, c2, unused, s_tot + par * kRec);
+        par ^= 1;
+        step.alpha.x = (conv[0] || !(c2[0] > 0.0f)) ? 0.0f : gam[0] / c2[0];
+        step.alpha.y = (conv[1] || !(c2[1] > 0.0f)) ? 0.0f : gam[1] / c2[1];
+        step.beta = make_float2(0.0f, 0.0f);
+        step.first = true;
+        need_w = false;
+      }
+
+      // ---- one CG step: state q -> q^1 (with the true residual of x' and
+      //      the sample at x' once the recursive residual is close) --------
+      const bool verify = (conv[0] || rr[0] <= kVerifyGate * rtol2 * bn2[0]) &&
+                          (conv[1] || rr[1] <= kVerifyGate * rtol2 * bn2[1]);
+      float c8[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      ff e = ff_zero();
+      if (verify) {
+        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, true>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn);
+        if (kEdges) {
+          for (int q2 = tid; q2 < a.nE; q2 += nth) {
+            const int2 ab = __ldg(a.edges + q2);
+            const CgNext na = cg_next(load_cg(cg[q], ab.x), __ldg(a.dinv + ab.x), step);
+            const CgNext nb2 = cg_next(load_cg(cg[q], ab.y), __ldg(a.dinv + ab.y), step);
+            e = ff_add_f(e, sample_edge(a, q2, ab, na.x, nb2.x));
+          }
+        }
+        warp_energy_store(e, a.epart + (size_t)(it + 1) * a.ewarps, gwarp);
+        block_record<8, false>(c8, ff_zero(), MY_REC, s_red);
+      } else {
+        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, false>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn);
+        block_record<8, false>(c8, e, MY_REC, s_red);
+      }
+      SYNC_OR_LEAVE();
+      ff unused;
+      grid_totals<8, false>(ALL_REC, nb, c8, unused, s_tot + par * kRec);
+      par ^= 1;
+      q ^= 1;
+      ++k;
+      rr[0] = c8[6];
+      rr[1] = c8[7];
+      if (verify) {
+        rt2[0] = c8[4];
+        rt2[1] = c8[5];
+        conv[0] = conv[0] || rt2[0] <= rtol2 * bn2[0];
+        conv[1] = conv[1] || rt2[1] <= rtol2 * bn2[1];
+        if (conv[0] && conv[1]) {
+          have_sample = true;   // the sample taken in this step is of the final x'
+          break;
+        }
+      }
+      bool restart = false;
+      float nal[2] = {0.0f, 0.0f}, nbe[2] = {0.0f, 0.0f};
+      const float al[2] = {step.alpha.x, step.alpha.y};
+      for (int c = 0; c < 2; ++c) {
+        if (conv[c]) continue;
+        const float gn = c8[c], dn = c8[2 + c];
+        const float be = gam[c] > 0.0f ? gn / gam[c] : 0.0f;
+        const float den = al[c] > 0.0f ? dn - be * gn / al[c] : 0.0f;
+        if (!(den > 0.0f) || !(gn > 0.0f)) restart = true;
+        if (verify && rr[c] < 1e-2f * rt2[c]) restart = true;   // FP32 recursion drifted
+        nal[c] = den > 0.0f ? gn / den : 0.0f;
+        nbe[c] = be;
+        gam[c] = gn;
+      }
+      if (restart && verify) {
+        // restart every unconverged component from the true residual:
+        // r = rt, z = D^-1 rt; w = A z is formed by the next need_w pass
+        float c2[2] = {0.0f, 0.0f};
+        for (int i = tid; i < nV; i += nth) {
+          float4* node = cg[q] + 3 * (size_t)i;
+          const float2 rt = a.rt[i];
+          float4 xz = node[0], pr = node[1];
+          const float di = __ldg(a.dinv + i);
+          if (!conv[0]) {
+            pr.z = rt.x;
+            xz.z = __fmul_rn(di, rt.x);
+          }
+          if (!conv[1]) {
+            pr.w = rt.y;
+            xz.w = __fmul_rn(di, rt.y);
+          }
+          node[0] = xz;
+          node[1] = pr;
+          c2[0] += pr.z * xz.z;
+          c2[1] += pr.w * xz.w;
+        }
+        block_record<2, false>(c2, ff_zero(), MY_REC, s_red);
+        SYNC_OR_LEAVE();
+        ff unused;
+        grid_totals<2, false>(ALL_REC, nb, c2, unused, s_tot + par * kRec);
+        par ^= 1;
+        gam[0] = c2[0];
+        gam[1] = c2[1];
+        rr[0] = rt2[0];
+        rr[1] = rt2[1];
+        need_w = true;
+      } else if (restart) {
+        // breakdown in the recursion without a true residual at hand: restart
+        // from the recursive residual, which is the current r
+        need_w = true;
+      } else {
+        step.alpha = make_float2(nal[0], nal[1]);
+        step.beta = make_float2(nbe[0], nbe[1]);
+        step.first = false;
+      }
+    }
+    if (lead) {
+      double rel = 0.0;
+      for (int c = 0; c < 2; ++c) {
+        const double qq = bn2[c] > 0.0f ? sqrt((double)rt2[c] / (double)bn2[c])
+                                        : (rt2[c] > 0.0f ? 1.0 : 0.0);
+        rel = qq > rel ? qq : rel;
+      }
+      if (hi < a.hist_cap) {
+        a.pcg_it_hist[hi] = k;
+        a.pcg_res_hist[hi] = rel;
+      }
+      a.last[1] = rel;
+      a.last[2] = (double)k;
+      if ((double)k > a.last[3]) a.last[3] = (double)k;
+      if (capped) {
+        a.last[4] += 1.0;
+        atomicOr(a.status, kStatusNotConverged);
+      }
+    }
+  }
+  // Hand the displacement back in u, and leave f (and F) describing it even
+  // when the last solve stopped at its cap (no reduction needed for that).
+  const DispCg disp{cg[q]};
+  for (int i = tid; i < nV; i += nth) a.u[i] = disp(i);
+  if (!have_sample && a.n_iters > 0) {
+    float2* Fn = a.F + (size_t)(a.n_iters & 1) * nV;
+    if (kEdges) {
+      // other nodes' x are final since the last barrier
+      for (int q2 = tid; q2 < a.nE; q2 += nth) {
+        const int2 ab = __ldg(a.edges + q2);
+        sample_edge(a, q2, ab, disp(ab.x), disp(ab.y));
+      }
+    } else {
+      for (int i = tid; i < nV; i += nth) {
+        float2 unusedF;
+        sample_node<FORM, GRAD>(a, i, disp(i), a.f + i, Fn + i, &unusedF);
+      }
+    }
+  }
+  return true;
+}
+
+#undef MY_REC
+#undef ALL_REC
+#undef SYNC_OR_LEAVE
+#undef FOR_NODES
+
+}  // namespace
+}  // namespace mreg

@@ -115,4 +115,68 @@ cudaError_t iterate_max_blocks(int form, int grad, int block, int* max_blocks_pe
 cudaError_t launch_iterate(int form, int grad, const IterArgs& a, int grid, int block,
                            cudaStream_t s);
 
+// ---------------------------------------------------------------- batched
+// Many registrations in one launch sequence.  Every per-kind array (pixels,
+// nodes, triangles, ...) of all pairs is packed into one buffer; the per-pair
+// IterArgs / WarpArgs / PairSetup records hold pointers into them.
+
+// Set-up inputs and outputs of one pair (step a0, node samples, pixel map).
+struct PairSetup {
+  const float* Re;
+  const float* Te;
+  float* tmpR;           // row-pass results of Re and Te
+  float* tmpT;
+  float* cRe;
+  float* cTe;
+  const float2* V;
+  const int* tri;
+  const int2* edges;
+  int* pix_tri;
+  float* ReV;
+  float* ReQ;
+  int W, H, nV, nT, nE;
+};
+
+struct BatchArgs {
+  const IterArgs* args;  // per pair
+  const int* order;      // pairs in the order the teams take them (largest first)
+  int n_pairs, n_iters;
+  int team_ctas;         // CTAs per team (thread-block cluster)
+  int ewarps;            // warps per team
+  int* queue;            // next position in order; zero before the launch
+  float* part;           // per team: 2 * team_ctas * kRec partial sums
+  float2* epart;         // per pair: (n_iters + 1) * ewarps energy partials
+};
+
+struct BatchSetupArgs {
+  const PairSetup* pairs;
+  int n_pairs;
+  const int* task_off[2];   // per pass (rows, columns): prefilter tasks per pair, prefix
+  const int* node_off;      // n_pairs + 1 prefix of nodes
+  const int* tri_off;       // n_pairs + 1 prefix of triangles
+  const int* edge_off;      // n_pairs + 1 prefix of edges
+  int tasks[2], nodes, tris, edges;
+};
+
+struct BatchWarpArgs {
+  const WarpArgs* pairs;    // part: unused (records go to rec)
+  const int2* tiles;        // (pair, first pixel) of each tile
+  const int* tile_off;      // n_pairs + 1 prefix of tiles
+  int n_tiles, n_pairs;
+  float* rec;               // one kRec record per tile
+  double* msd;              // per pair
+};
+
+constexpr int kBatchTilePx = 4096;   // pixels per warp tile
+
+cudaError_t batch_prepare(int form, int grad, int block);
+cudaError_t batch_setup(const BatchSetupArgs& a, bool edges, cudaStream_t s);
+cudaError_t batch_pixel_map(const BatchSetupArgs& a, int* pix_all, int64_t n_px, cudaStream_t s);
+cudaError_t batch_count_uncovered(const BatchSetupArgs& a, const int64_t* px_off, int64_t n_px,
+                                  const int* pix_tri, int* counts, cudaStream_t s);
+cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int* max_teams);
+cudaError_t batch_launch_iterate(int form, int grad, const BatchArgs& b, int n_teams, int block,
+                                 int hist_cap, cudaStream_t s);
+cudaError_t batch_warp_msd(const BatchWarpArgs& a, cudaStream_t s);
+
 }  // namespace mreg

@@ -1,0 +1,214 @@
+// Device pieces of the set-up steps and of the warp, shared by the
+// one-pair launchers (prefilter.cu, warp.cu) and the batched engine
+// (batch.cu).
+//
+// Prefilter (step a0; abstract and Sec. 2.1: both images are interpolated by
+// splines; the coefficients come from the recursive filter of M. Unser,
+// IEEE SPM 1999: pole z1 = sqrt(3)-2, gain 6, mirror boundary).
+//
+// One warp filters 32 lines (rows, then columns) over one segment of kSegLen
+// outputs.  The causal recursion c+(n) = 6 s(n) + z1 c+(n-1) and the
+// anticausal recursion c-(n) = z1 (c-(n+1) - c+(n)) run lane-per-line over a
+// window staged in shared memory.  The window extends kWarm samples beyond
+// the segment on each side: the state entering the window is taken as 0,
+// whose effect decays as |z1|^kWarm ~ 1.9e-14, far below FP32 resolution.
+// Where the window reaches the image border the exact mirror-boundary
+// initial values are used instead, so every line matches the full-length
+// recursion.  Windows are staged transposed (line-major in the lane index)
+// so that both the global loads/stores and the lane-per-line shared-memory
+// accesses are conflict-free.
+//
+// Pixel map (set-up of step a4): every pixel centre gets the smallest-index
+// closed triangle of the undeformed mesh that contains it.  The inside test
+// uses FP64 orientation determinants, each operation rounded separately (no
+// FMA), formed from the lower-numbered to the higher-numbered node of each
+// edge so that neighbouring triangles classify points on their shared edge
+// alike.
+#pragma once
+
+#include "device_common.cuh"
+#include "mreg_internal.h"
+
+namespace mreg {
+namespace {
+
+constexpr int kSegLen = 64;
+constexpr int kWarm = 24;
+constexpr int kWin = kSegLen + 2 * kWarm;
+constexpr int kPitch = 33;                 // 32 lines + 1 pad word
+constexpr int kWarpsPerBlock = 4;
+constexpr size_t kSmemPerWarp = (size_t)kWin * kPitch * sizeof(float);
+
+
+// Exact causal initial value c+(0) = sum_k z1^k c~(k) over the mirror-periodic
+// extension (period 2N-2), for short lines; the forward sum truncated after
+// kWarm terms otherwise (error |z1|^kWarm).  t: line in shared memory with
+// stride kPitch, already multiplied by the gain.
+__device__ float causal_init(const float* t, int N) {
+  const float z = kZ1;
+  if (N > kWarm) {
+    float acc = 0.0f, zk = 1.0f;
+    for (int k = 0; k < kWarm; ++k) {
+      acc += zk * t[k * kPitch];
+      zk *= z;
+    }
+    return acc;
+  }
+  // N <= kWarm: one full period, then the geometric factor.
+  const int period = 2 * N - 2;
+  float acc = 0.0f, zk = 1.0f;
+  for (int k = 0; k < period; ++k) {
+    const int j = k < N ? k : period - k;
+    acc += zk * t[j * kPitch];
+    zk *= z;
+  }
+  return acc / (1.0f - zk);   // zk == z^period here
+}
+
+// Number of warp tasks (32 lines x one segment) of one pass.
+template <int DIR>
+__host__ __device__ __forceinline__ int prefilter_tasks(int W, int H) {
+  const int N = DIR == 0 ? W : H, nlines = DIR == 0 ? H : W;
+  return ((nlines + 31) / 32) * ((N + kSegLen - 1) / kSegLen);
+}
+
+// One warp task gw < prefilter_tasks<DIR>(W, H) of a pass.  DIR 0: lines are
+// rows (recursion along x).  DIR 1: lines are columns.  tile: this warp's
+// kWin x kPitch floats of shared memory.  Called by all 32 lanes.
+template <int DIR>
+__device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int64_t in_stride,
+                                               float* __restrict__ out, int64_t out_stride, int W,
+                                               int H, int gw, float* tile) {
+  const int lane = threadIdx.x & 31;
+  const int N = DIR == 0 ? W : H;            // line length
+  const int nlines = DIR == 0 ? H : W;
+  const int nseg = (N + kSegLen - 1) / kSegLen;
+  const int line0 = (gw / nseg) * 32;
+  const int seg = gw % nseg;
+  const int s0 = seg * kSegLen, s1 = min(N, s0 + kSegLen);
+  const int w0 = max(0, s0 - kWarm), w1 = min(N, s1 + kWarm);
+  const int wn = w1 - w0;
+  const int nl = min(32, nlines - line0);
+  const float gain = 6.0f;
+
+  // stage the window: tile[k * kPitch + l] = gain * sample k of line l
+  if (DIR == 0) {
+    for (int l = 0; l < nl; ++l) {
+      const float* src = in + (int64_t)(line0 + l) * in_stride + w0;
+      for (int k = lane; k < wn; k += 32) tile[k * kPitch + l] = gain * src[k];
+    }
+  } else {
+    if (lane < nl) {
+      for (int k = 0; k < wn; ++k)
+        tile[k * kPitch + lane] = gain * in[(int64_t)(w0 + k) * in_stride + line0 + lane];
+    }
+  }
+  __syncwarp();
+
+  if (lane < nl) {
+    float* t = tile + lane;
+    const float z = kZ1;
+    // causal pass, in place
+    float cp = (w0 == 0) ? causal_init(t, N) : t[0];
+    t[0] = cp;
+    for (int k = 1; k < wn; ++k) {
+      cp = t[k * kPitch] + z * cp;
+      t[k * kPitch] = cp;
+    }
+    // anticausal pass, in place
+    float cm;
+    if (w1 == N) {
+      cm = (z / (z * z - 1.0f)) * (t[(wn - 1) * kPitch] + z * t[(wn - 2) * kPitch]);
+    } else {
+      cm = -z * t[(wn - 1) * kPitch];
+    }
+    t[(wn - 1) * kPitch] = cm;
+    for (int k = wn - 2; k >= 0; --k) {
+      cm = z * (cm - t[k * kPitch]);
+      t[k * kPitch] = cm;
+    }
+  }
+  __syncwarp();
+
+  // write the segment's outputs
+  const int o0 = s0 - w0, on = s1 - s0;
+  if (DIR == 0) {
+    for (int l = 0; l < nl; ++l) {
+      float* dst = out + (int64_t)(line0 + l) * out_stride + s0;
+      for (int k = lane; k < on; k += 32) dst[k] = tile[(o0 + k) * kPitch + l];
+    }
+  } else {
+    if (lane < nl) {
+      for (int k = 0; k < on; ++k)
+        out[(int64_t)(s0 + k) * out_stride + line0 + lane] = tile[(o0 + k) * kPitch + lane];
+    }
+  }
+}
+
+__device__ __forceinline__ double orient_rn(double ax, double ay, double bx, double by, double px,
+                                            double py) {
+  const double t1 = __dmul_rn(__dsub_rn(bx, ax), __dsub_rn(py, ay));
+  const double t2 = __dmul_rn(__dsub_rn(by, ay), __dsub_rn(px, ax));
+  return __dsub_rn(t1, t2);
+}
+
+__device__ __forceinline__ double edge_side(const float2* __restrict__ V, int a, int b, double px,
+                                            double py) {
+  const int lo = min(a, b), hi = max(a, b);
+  const float2 A = __ldg(V + lo), B = __ldg(V + hi);
+  const double s = orient_rn(A.x, A.y, B.x, B.y, px, py);
+  return a < b ? s : -s;
+}
+
+// Marks every pixel centre inside closed triangle t (smallest index wins).
+__device__ __forceinline__ void pixel_map_triangle(const float2* __restrict__ V,
+                                                   const int* __restrict__ tri, int t, int W, int H,
+                                                   int* __restrict__ pix) {
+  const int a = __ldg(tri + 3 * t), b = __ldg(tri + 3 * t + 1), c = __ldg(tri + 3 * t + 2);
+  const float2 A = __ldg(V + a), B = __ldg(V + b), C = __ldg(V + c);
+  const int x0 = max(0, (int)ceilf(fminf(A.x, fminf(B.x, C.x))));
+  const int x1 = min(W - 1, (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x))));
+  const int y0 = max(0, (int)ceilf(fminf(A.y, fminf(B.y, C.y))));
+  const int y1 = min(H - 1, (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y))));
+  for (int y = y0; y <= y1; ++y) {
+    const double py = (double)y;
+    for (int x = x0; x <= x1; ++x) {
+      const double px = (double)x;
+      if (edge_side(V, a, b, px, py) >= 0.0 && edge_side(V, b, c, px, py) >= 0.0 &&
+          edge_side(V, c, a, px, py) >= 0.0)
+        atomicMin(pix + (int64_t)y * W + x, t);
+    }
+  }
+}
+
+// Registered value R = Te(x + u(x)) at pixel p and its difference with Re
+// (step a4): P1 interpolation of the owning triangle's node displacements,
+// then the cubic B-spline of Te.  Returns false for a pixel without an owner
+// (excluded by the coverage check at set-up).
+__device__ __forceinline__ bool warp_pixel(const WarpArgs& a, int64_t p, float& R, float& d) {
+  const int W = a.W, H = a.H;
+  const int t = __ldg(a.pix_tri + p);
+  if ((unsigned)t >= (unsigned)a.nT) return false;
+  const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+  const int ia = __ldg(a.tri + 3 * t), ib = __ldg(a.tri + 3 * t + 1), ic = __ldg(a.tri + 3 * t + 2);
+  const float2 Va = __ldg(a.V + ia), Vb = __ldg(a.V + ib), Vc = __ldg(a.V + ic);
+  const float2 ua = __ldg(a.u + ia), ub = __ldg(a.u + ib), uc = __ldg(a.u + ic);
+  // corner positions relative to the pixel (exact differences)
+  const float fx = (float)x, fy = (float)y;
+  const float ax = Va.x - fx, ay = Va.y - fy;
+  const float bx = Vb.x - fx, by = Vb.y - fy;
+  const float cx = Vc.x - fx, cy = Vc.y - fy;
+  const float sa = bx * cy - by * cx;   // twice the area of (x, b, c)
+  const float sb = cx * ay - cy * ax;   // (x, c, a)
+  const float sc = ax * by - ay * bx;   // (x, a, b)
+  const float inv = 1.0f / (sa + sb + sc);
+  const float ux = (sa * ua.x + sb * ub.x + sc * uc.x) * inv;
+  const float uy = (sa * ua.y + sb * ub.y + sc * uc.y) * inv;
+  R = a.cTe16 ? spline_sample<false>(a.cTe16, W, H, x, y, ux, uy, nullptr, nullptr)
+              : spline_sample<false>(a.cTe, W, H, x, y, ux, uy, nullptr, nullptr);
+  d = R - __ldg(a.Re + p);
+  return true;
+}
+
+}  // namespace
+}  // namespace mreg

@@ -15,26 +15,10 @@
 // the sums are float-float (hi + lo FP32 pairs), the final mean FP64.
 #include <climits>
 
-#include "device_common.cuh"
-#include "mreg_internal.h"
+#include "setup_common.cuh"
 
 namespace mreg {
 namespace {
-
-__device__ __forceinline__ double orient_rn(double ax, double ay, double bx, double by, double px,
-                                            double py) {
-  const double t1 = __dmul_rn(__dsub_rn(bx, ax), __dsub_rn(py, ay));
-  const double t2 = __dmul_rn(__dsub_rn(by, ay), __dsub_rn(px, ax));
-  return __dsub_rn(t1, t2);
-}
-
-__device__ __forceinline__ double edge_side(const float2* __restrict__ V, int a, int b, double px,
-                                            double py) {
-  const int lo = min(a, b), hi = max(a, b);
-  const float2 A = __ldg(V + lo), B = __ldg(V + hi);
-  const double s = orient_rn(A.x, A.y, B.x, B.y, px, py);
-  return a < b ? s : -s;
-}
 
 __global__ void k_fill(int* __restrict__ p, int64_t n, int v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -44,23 +28,8 @@ __global__ void k_fill(int* __restrict__ p, int64_t n, int v) {
 
 __global__ void k_pixel_map(const float2* __restrict__ V, const int* __restrict__ tri, int nT, int W,
                             int H, int* __restrict__ pix) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
-    const int a = __ldg(tri + 3 * t), b = __ldg(tri + 3 * t + 1), c = __ldg(tri + 3 * t + 2);
-    const float2 A = __ldg(V + a), B = __ldg(V + b), C = __ldg(V + c);
-    const int x0 = max(0, (int)ceilf(fminf(A.x, fminf(B.x, C.x))));
-    const int x1 = min(W - 1, (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x))));
-    const int y0 = max(0, (int)ceilf(fminf(A.y, fminf(B.y, C.y))));
-    const int y1 = min(H - 1, (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y))));
-    for (int y = y0; y <= y1; ++y) {
-      const double py = (double)y;
-      for (int x = x0; x <= x1; ++x) {
-        const double px = (double)x;
-        if (edge_side(V, a, b, px, py) >= 0.0 && edge_side(V, b, c, px, py) >= 0.0 &&
-            edge_side(V, c, a, px, py) >= 0.0)
-          atomicMin(pix + (int64_t)y * W + x, t);
-      }
-    }
-  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x)
+    pixel_map_triangle(V, tri, t, W, H, pix);
 }
 
 __global__ void k_count_equal(const int* __restrict__ p, int64_t n, int v, int* count) {
@@ -76,32 +45,13 @@ constexpr int kWarpBlock = 256;
 
 __global__ void __launch_bounds__(kWarpBlock) k_warp_msd(const WarpArgs a) {
   __shared__ float s_red[kMaxWarps * kRec];
-  const int W = a.W, H = a.H;
-  const int64_t n = (int64_t)W * H;
+  const int64_t n = (int64_t)a.W * a.H;
   ff acc = ff_zero();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const int t = __ldg(a.pix_tri + p);
-    if ((unsigned)t >= (unsigned)a.nT) continue;   // excluded by the coverage check at set-up
-    const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
-    const int ia = __ldg(a.tri + 3 * t), ib = __ldg(a.tri + 3 * t + 1), ic = __ldg(a.tri + 3 * t + 2);
-    const float2 Va = __ldg(a.V + ia), Vb = __ldg(a.V + ib), Vc = __ldg(a.V + ic);
-    const float2 ua = __ldg(a.u + ia), ub = __ldg(a.u + ib), uc = __ldg(a.u + ic);
-    // corner positions relative to the pixel (exact differences)
-    const float fx = (float)x, fy = (float)y;
-    const float ax = Va.x - fx, ay = Va.y - fy;
-    const float bx = Vb.x - fx, by = Vb.y - fy;
-    const float cx = Vc.x - fx, cy = Vc.y - fy;
-    const float sa = bx * cy - by * cx;   // twice the area of (x, b, c)
-    const float sb = cx * ay - cy * ax;   // (x, c, a)
-    const float sc = ax * by - ay * bx;   // (x, a, b)
-    const float inv = 1.0f / (sa + sb + sc);
-    const float ux = (sa * ua.x + sb * ub.x + sc * uc.x) * inv;
-    const float uy = (sa * ua.y + sb * ub.y + sc * uc.y) * inv;
-    const float R = a.cTe16 ? spline_sample<false>(a.cTe16, W, H, x, y, ux, uy, nullptr, nullptr)
-                            : spline_sample<false>(a.cTe, W, H, x, y, ux, uy, nullptr, nullptr);
+    float R, d;
+    if (!warp_pixel(a, p, R, d)) continue;
     if (a.out) a.out[p] = R;
-    const float d = R - __ldg(a.Re + p);
     acc = ff_add(acc, ff_prod(d, d));
   }
   float none[1] = {0.0f};

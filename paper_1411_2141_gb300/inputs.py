@@ -39,7 +39,7 @@ import numpy as np
 
 __all__ = [
     "CaseSpec", "Case", "CONFIGS", "config_spec", "make_case", "make_mesh",
-    "make_phantom_pair", "batched_specs",
+    "make_phantom_pair", "batched_specs", "make_cases",
 ]
 
 
@@ -223,6 +223,71 @@ def _morton_key(x, y, bits=16):
     return key
 
 
+def _thin_min_spacing(bnd, cand, n_int, spacing, W, H):
+    """Greedy minimum-spacing thinning: visiting the candidates in priority
+    order, keep one when no boundary point and no kept candidate lies closer
+    than ``spacing``; stop after ``n_int`` kept.  Returns the boundary points
+    followed by the kept candidates, in that order.
+
+    Candidates are distinct pixel centres jittered by at most 0.25 px, so two
+    of them can only conflict within a small pixel neighbourhood.  The greedy
+    result is computed in rounds: a candidate is rejected once a conflicting
+    candidate of higher priority is kept, and kept once every conflicting
+    candidate of higher priority is rejected.  Each decision depends only on
+    higher-priority candidates, so this gives exactly the sequential result.
+    """
+    m = len(cand)
+    sp2 = spacing * spacing
+    if m == 0 or n_int == 0:
+        return np.asarray(bnd, dtype=np.float64)
+    ix = np.rint(cand[:, 0]).astype(np.int64)
+    iy = np.rint(cand[:, 1]).astype(np.int64)
+    R = int(math.ceil(spacing + 0.5))
+    rank = -np.ones((H, W), np.int64)
+    rank[iy, ix] = np.arange(m)
+    src, dst = [], []
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            if dx == 0 and dy == 0:
+                continue
+            jx, jy = ix + dx, iy + dy
+            ok = (jx >= 0) & (jx < W) & (jy >= 0) & (jy < H)
+            j = np.full(m, -1, np.int64)
+            j[ok] = rank[jy[ok], jx[ok]]
+            i = np.arange(m)
+            sel = (j >= 0) & (j < i)
+            d2 = ((cand[j[sel], 0] - cand[sel, 0]) ** 2 + (cand[j[sel], 1] - cand[sel, 1]) ** 2)
+            close = d2 < sp2
+            src.append(i[sel][close])
+            dst.append(j[sel][close])
+    src = np.concatenate(src)
+    dst = np.concatenate(dst)
+    # conflicts with the (always kept) boundary points
+    bmap = np.zeros((H, W), bool)
+    bx = np.rint(bnd[:, 0]).astype(np.int64)
+    by = np.rint(bnd[:, 1]).astype(np.int64)
+    bmap[by, bx] = True
+    state = np.zeros(m, np.int8)   # 0 undecided, 1 kept, 2 rejected
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            jx, jy = ix + dx, iy + dy
+            ok = (jx >= 0) & (jx < W) & (jy >= 0) & (jy < H)
+            hit = np.zeros(m, bool)
+            hit[ok] = bmap[jy[ok], jx[ok]]
+            d2 = (jx - cand[:, 0]) ** 2 + (jy - cand[:, 1]) ** 2
+            state[hit & (d2 < sp2)] = 2
+    while True:
+        und = state == 0
+        if not und.any():
+            break
+        kept_nb = np.bincount(src, weights=(state[dst] == 1), minlength=m) > 0
+        open_nb = np.bincount(src, weights=(state[dst] == 0), minlength=m) > 0
+        state[und & kept_nb] = 2
+        state[und & ~kept_nb & ~open_nb] = 1
+    kept = np.flatnonzero(state == 1)[:n_int]
+    return np.concatenate([np.asarray(bnd, dtype=np.float64), cand[kept]], axis=0)
+
+
 def make_mesh(Te: np.ndarray, n_nodes: int, seed: int, spacing: float = 1.0,
               boundary_step: int = 16):
     """Density-sampled Delaunay mesh of the image domain ``[0,W-1]x[0,H-1]``."""
@@ -245,34 +310,8 @@ def make_mesh(Te: np.ndarray, n_nodes: int, seed: int, spacing: float = 1.0,
     order = np.argsort(-keys, kind="stable")[:m]
     cand = np.stack([ix[order], iy[order]], axis=1).astype(np.float64)
     cand += rng.uniform(-0.25, 0.25, size=cand.shape)
-    # greedy minimum-spacing thinning on a unit hash grid
-    grid: dict[tuple[int, int], list[int]] = {}
-    pts = [tuple(p) for p in bnd]
-    for k, (px, py) in enumerate(pts):
-        grid.setdefault((int(px), int(py)), []).append(k)
-    sp2 = spacing * spacing
-    taken = 0
-    for px, py in cand:
-        if taken >= n_int:
-            break
-        cx, cy = int(px), int(py)
-        ok = True
-        for gy_ in (cy - 1, cy, cy + 1):
-            for gx_ in (cx - 1, cx, cx + 1):
-                for k in grid.get((gx_, gy_), ()):
-                    qx, qy = pts[k]
-                    if (qx - px) ** 2 + (qy - py) ** 2 < sp2:
-                        ok = False
-                        break
-                if not ok:
-                    break
-            if not ok:
-                break
-        if ok:
-            grid.setdefault((cx, cy), []).append(len(pts))
-            pts.append((px, py))
-            taken += 1
-    P = np.asarray(pts, dtype=np.float32).astype(np.float64)
+    P = _thin_min_spacing(bnd, cand, n_int, spacing, W, H)
+    P = P.astype(np.float32).astype(np.float64)
     tri = Delaunay(P).simplices.astype(np.int64)
     a = P[tri]
     area2 = ((a[:, 1, 0] - a[:, 0, 0]) * (a[:, 2, 1] - a[:, 0, 1])
@@ -303,3 +342,27 @@ def make_case(spec: CaseSpec) -> Case:
     Re, Te, d = make_phantom_pair(spec)
     V, T = make_mesh(Te, spec.n_nodes, spec.seed)
     return Case(spec=spec, Re=Re, Te=Te, V=V, T=T, d=d)
+
+
+def make_cases(specs, processes: int | None = None) -> list[Case]:
+    """``make_case`` for many specs, in worker processes (``spawn`` start
+    method, safe after CUDA has been initialised in the caller).  The result
+    does not depend on the number of workers."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    specs = list(specs)
+    if processes is None:
+        processes = min(len(specs), os.cpu_count() or 1, 16)
+    if processes <= 1 or len(specs) <= 1:
+        return [make_case(s) for s in specs]
+    # largest first, so that the pool finishes evenly
+    order = sorted(range(len(specs)), key=lambda k: -specs[k].side)
+    out: list = [None] * len(specs)
+    with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+        futs = {ex.submit(make_case, specs[k]): k for k in order}
+        for f in cf.as_completed(futs):
+            out[futs[f]] = f.result()
+    return out
+

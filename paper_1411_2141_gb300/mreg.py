@@ -76,7 +76,7 @@ class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
-                ("coeff_bf16", C.c_int32)]
+                ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -90,7 +90,9 @@ class mreg_stats_t(C.Structure):
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
            "mreg_msd", "mreg_energy", "mreg_get_u", "mreg_set_u", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
-           "mreg_prefilter_noalloc"]
+           "mreg_prefilter_noalloc", "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
+           "mreg_batch_shape", "mreg_batch_iterate_ms", "mreg_batch_msd", "mreg_batch_get_field",
+           "mreg_batch_stats", "mreg_batch_destroy"]
 
 NOALLOC_MAX_PIXELS = 1024 * 1024
 
@@ -131,6 +133,18 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_last_error": ([], C.c_char_p),
         "mreg_version": ([], i32),
         "mreg_prefilter_noalloc": ([vp, i64, vp, i32, i32, vp], i32),
+        "mreg_batch_create": ([i32, C.POINTER(mreg_mesh), C.POINTER(mreg_image),
+                               C.POINTER(mreg_image), dbl, dbl, C.POINTER(mreg_options), vp,
+                               C.POINTER(vp)], i32),
+        "mreg_batch_run": ([vp, i32, vp], i32),
+        "mreg_batch_tune": ([vp, i32, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)],
+                            i32),
+        "mreg_batch_shape": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
+        "mreg_batch_iterate_ms": ([vp, C.POINTER(C.c_float)], i32),
+        "mreg_batch_msd": ([vp, C.POINTER(dbl), vp], i32),
+        "mreg_batch_get_field": ([vp, i32, i32, vp, i32, C.POINTER(i64), vp], i32),
+        "mreg_batch_stats": ([vp, i32, C.POINTER(mreg_stats_t), vp], i32),
+        "mreg_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -185,7 +199,7 @@ def default_options() -> mreg_options:
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
-                 coeff_bf16=False) -> mreg_options:
+                 coeff_bf16=False, team_ctas=0) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -200,6 +214,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.grid_blocks = int(grid_blocks)
     o.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     o.coeff_bf16 = int(bool(coeff_bf16))
+    o.team_ctas = int(team_ctas)
     return o
 
 
@@ -336,6 +351,133 @@ class Registration:
         st = load().mreg_stats(self._h, C.byref(s), _stream_ptr(stream))
         if check:
             _check(st, "mreg_stats")
+        d = {k: getattr(s, k) for k, _ in mreg_stats_t._fields_}
+        d["status"] = st
+        return d
+
+
+_FIELD_DTYPES = {MREG_FIELD_PIXEL_TRI: np.int32, MREG_FIELD_PCG_ITERS: np.int32,
+                 MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64,
+                 MREG_FIELD_COEF_TE_BF16: np.uint16}
+
+
+class Batch:
+    """Many registration problems registered together (the batched engine).
+
+    ``pairs`` is a sequence of ``(V, T, Re, Te)``; every pair shares
+    ``alpha``, ``tau`` and the options."""
+
+    def __init__(self, pairs, alpha: float, tau: float, options: mreg_options | None = None,
+                 stream=None, **kw):
+        lib = load()
+        if options is None:
+            options = make_options(**kw)
+        pairs = list(pairs)
+        n = len(pairs)
+        if n < 1:
+            raise ValueError("need at least one pair")
+        keep: list = []
+        meshes = (mreg_mesh * n)()
+        res = (mreg_image * n)()
+        tes = (mreg_image * n)()
+        self.n_nodes, self.shapes = [], []
+        for k, (V, T, Re, Te) in enumerate(pairs):
+            Vh = np.ascontiguousarray(V, dtype=np.float32)
+            Th = np.ascontiguousarray(T, dtype=np.int32)
+            if Vh.ndim != 2 or Vh.shape[1] != 2 or Th.ndim != 2 or Th.shape[1] != 3:
+                raise ValueError(f"pair {k}: V must be (n, 2) and T (m, 3)")
+            keep += [Vh, Th]
+            meshes[k] = mreg_mesh(Vh.shape[0], Th.shape[0],
+                                  Vh.ctypes.data_as(C.POINTER(C.c_float)),
+                                  Th.ctypes.data_as(C.POINTER(C.c_int32)))
+            res[k] = _image(Re, keep)
+            tes[k] = _image(Te, keep)
+            self.n_nodes.append(int(Vh.shape[0]))
+            self.shapes.append((int(res[k].height), int(res[k].width)))
+        h = C.c_void_p()
+        self._h = None
+        _check(lib.mreg_batch_create(n, meshes, res, tes, float(alpha), float(tau),
+                                     C.byref(options), _stream_ptr(stream), C.byref(h)),
+               "mreg_batch_create")
+        self._h = h
+        self.n_pairs = n
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.mreg_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, n_iters: int, stream=None):
+        _check(load().mreg_batch_run(self._h, int(n_iters), _stream_ptr(stream)), "mreg_batch_run")
+
+    def tune(self, n_iters: int, stream=None):
+        """Autotune the team shape; returns (team_ctas, block_size, times)
+        with times[(ctas, block)] in ms (None where the shape is skipped)."""
+        c, k = C.c_int32(), C.c_int32()
+        t = (C.c_float * 12)()
+        _check(load().mreg_batch_tune(self._h, int(n_iters), _stream_ptr(stream), C.byref(c),
+                                      C.byref(k), t), "mreg_batch_tune")
+        times = {}
+        for i, ctas in enumerate((1, 2, 4, 8)):
+            for j, blk in enumerate((128, 256, 512)):
+                v = float(t[i * 3 + j])
+                times[(ctas, blk)] = v if v >= 0 else None
+        return c.value, k.value, times
+
+    def shape(self):
+        c, k, n = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().mreg_batch_shape(self._h, C.byref(c), C.byref(k), C.byref(n)),
+               "mreg_batch_shape")
+        return c.value, k.value, n.value
+
+    def iterate_ms(self) -> float:
+        """Device time of the iteration kernel in the last run (ms)."""
+        v = C.c_float()
+        _check(load().mreg_batch_iterate_ms(self._h, C.byref(v)), "mreg_batch_iterate_ms")
+        return v.value
+
+    def msd(self, stream=None) -> np.ndarray:
+        out = np.empty(self.n_pairs, np.float64)
+        _check(load().mreg_batch_msd(self._h, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     _stream_ptr(stream)), "mreg_batch_msd")
+        return out
+
+    def get_field(self, pair: int, field: int, stream=None) -> np.ndarray:
+        lib = load()
+        n = C.c_int64()
+        _check(lib.mreg_batch_get_field(self._h, int(pair), field, None, 0, C.byref(n),
+                                        _stream_ptr(stream)), "mreg_batch_get_field")
+        out = np.empty(n.value, _FIELD_DTYPES.get(field, np.float32))
+        if n.value:
+            _check(lib.mreg_batch_get_field(self._h, int(pair), field, out.ctypes.data, 0, None,
+                                            _stream_ptr(stream)), "mreg_batch_get_field")
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
+            out = out.reshape(-1, 2)
+        elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
+                field == MREG_FIELD_COEF_TE_BF16 and n.value):
+            out = out.reshape(self.shapes[pair])
+        return out
+
+    def get_u(self, pair: int, stream=None) -> np.ndarray:
+        return self.get_field(pair, MREG_FIELD_U, stream)
+
+    def stats(self, pair: int, stream=None, check: bool = True) -> dict:
+        s = mreg_stats_t()
+        st = load().mreg_batch_stats(self._h, int(pair), C.byref(s), _stream_ptr(stream))
+        if check:
+            _check(st, "mreg_batch_stats")
         d = {k: getattr(s, k) for k, _ in mreg_stats_t._fields_}
         d["status"] = st
         return d

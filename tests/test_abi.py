@@ -109,3 +109,25 @@ def test_clockwise_triangles_are_accepted_until_device_setup(lib):
     V, T = _mesh_square()
     img = np.zeros((6, 8), np.float32)
     _expect(mreg.MREG_ERR_CUDA, lambda: _create(V, T[:, [0, 2, 1]], img, img))
+
+
+def test_batch_host_validation_errors(lib):
+    """Argument errors of the batched engine are found before any CUDA call
+    and name the failing pair."""
+    V, T = _mesh_square()
+    img = np.zeros((6, 8), np.float32)
+    E = mreg
+    good = (V, T, img, img)
+    _expect(E.MREG_ERR_SIZE_MISMATCH,
+            lambda: mreg.Batch([good, (V, T, img, np.zeros((6, 9), np.float32))], 0.1, 1.0))
+    with pytest.raises(mreg.MregError, match="pair 2"):
+        mreg.Batch([good, good, (V, T, img, np.zeros((6, 9), np.float32))], 0.1, 1.0)
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: mreg.Batch([good], 0.1, 1.0, team_ctas=3))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: mreg.Batch([good], -0.1, 1.0))
+    _expect(E.MREG_ERR_BAD_MESH,
+            lambda: mreg.Batch([good, (V, np.array([[0, 1, 9]], np.int32), img, img)], 0.1, 1.0))
+    h = C.c_void_p()
+    assert lib.mreg_batch_create(0, None, None, None, 0.1, 1.0, None, None,
+                                 C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
+    assert lib.mreg_batch_run(None, 1, None) == mreg.MREG_ERR_INVALID_ARG
+    lib.mreg_batch_destroy(None)
