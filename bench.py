@@ -53,6 +53,12 @@ def parse():
     p.add_argument("--grad", default="G0", choices=["G0", "G1"])
     p.add_argument("--coeff", default="fp32", choices=["fp32", "bf16"],
                    help="storage of Te's spline coefficients (bf16: the precision form)")
+    p.add_argument("--team", default=None,
+                   help="config 3: fixed team shape 'ctas,block[,blocks_per_sm]' instead of "
+                        "the autotuner")
+    p.add_argument("--single", action="store_true",
+                   help="config 3: register the pairs one after another with the one-pair "
+                        "engine (the plain FP32 form) instead of the batched engine")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -399,7 +405,8 @@ def batch_workload_config(args, cases, shape=None):
            "l2": "flushed between timed steps (256 MiB write); the packed batch (~1.3 GB) exceeds L2",
            "parallelism": f"replicas x{args.gpus} (the whole batch per GPU per step)"}
     if shape is not None:
-        cfg["team"] = {"ctas": shape[0], "block": shape[1], "teams": shape[2]}
+        cfg["team"] = {"ctas": shape[0], "block": shape[1], "blocks_per_sm": shape[2],
+                       "teams": shape[3]}
     return cfg
 
 
@@ -419,6 +426,72 @@ def oracle_batch_time(cases, mode: str, grad: str, n_sample_pairs: int = 8, samp
     return t_pick * scale, pick, sample_iters
 
 
+def run_ours_batch_single(args, rank, world, local_rank):
+    """The batched workload through the one-pair engine: every pair has its
+    own handle (created before timing); a step registers all pairs one after
+    another (reset + iterations + warp/MSD each), as the plain FP32 form
+    would."""
+    import torch
+    from paper_1411_2141_gb300 import mreg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    mreg.load()
+    cases = batch_cases()
+    n_iter = cases[0].spec.n_iter
+    stream = torch.cuda.current_stream()
+    regs = [mreg.Registration(c.V, c.T, torch.from_numpy(c.Re).to(dev),
+                              torch.from_numpy(c.Te).to(dev), c.spec.alpha, c.spec.tau,
+                              mode=args.mode, grad=args.grad, coeff_bf16=args.coeff == "bf16",
+                              stream=stream) for c in cases]
+    msd_dev = torch.empty(len(cases), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        for k, r in enumerate(regs):
+            r.reset(stream)
+            r.step(n_iter, stream)
+            r.warp(None, msd_dev[k:k + 1], stream)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        one_step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_s = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, world, dev)
+    if rank != 0:
+        return
+    value = whole_job_rate(args.steps * len(cases), world, total_s)
+    cfg = batch_workload_config(args, cases)
+    cfg["engine"] = "one-pair grid engine, pairs in sequence (the plain FP32 form)"
+    line = {
+        "metric": "registrations/s", "value": value, "unit": "registrations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "node_iters_per_s": value / len(cases) * sum(c.n_nodes for c in cases) * n_iter,
+        "msd_mean": float(msd_dev.double().mean().item()), "clocks": clk,
+        "gpu_launches": sum(launches_per_registration(args, n_iter) for _ in cases) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    for r in regs:
+        r.close()
+
+
 def run_ours_batch(args, rank, world, local_rank):
     import torch
     from paper_1411_2141_gb300 import mreg
@@ -433,9 +506,18 @@ def run_ours_batch(args, rank, world, local_rank):
     pairs = [(c.V, c.T, c.Re, c.Te) for c in cases]
     b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode, grad=args.grad,
                    coeff_bf16=bf16, stream=stream)
-    t0 = time.perf_counter()
-    ctas, block, tune_ms = b.tune(n_iter, stream)
-    tune_s = time.perf_counter() - t0
+    if args.team:
+        vals = [int(x) for x in args.team.split(",")]
+        ctas, block, per_sm = (vals + [1])[:3]
+        b.close()
+        b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
+                       grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
+                       team_blocks_per_sm=per_sm, stream=stream)
+        tune_s, tune_ms = 0.0, {}
+    else:
+        t0 = time.perf_counter()
+        (ctas, block, per_sm), tune_ms = b.tune(n_iter, stream)
+        tune_s = time.perf_counter() - t0
     shape = b.shape()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -483,7 +565,7 @@ def run_ours_batch(args, rank, world, local_rank):
         def e2e_once():
             with mreg.Batch(pinned, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
                             grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
-                            stream=stream) as bb:
+                            team_blocks_per_sm=per_sm, stream=stream) as bb:
                 bb.run(n_iter, stream)
                 m = bb.msd(stream)
                 us = [bb.get_u(k, stream) for k in range(len(cases))]
@@ -522,8 +604,9 @@ def run_ours_batch(args, rank, world, local_rank):
         "msd_mean": float(msd.mean()), "msd_ratio_mean": float((msd / before).mean()),
         "cg_iters_mean": float(np.mean(cg)),
         "iteration_kernel_ms": it_ms,
-        "autotune": {"seconds": tune_s, "chosen": [ctas, block],
-                     "ms": {f"{c}x{k}": v for (c, k), v in tune_ms.items()}},
+        "autotune": ({"seconds": tune_s, "chosen": [ctas, block, per_sm],
+                      "ms": {f"{c}x{k}/{m}": v for (c, k, m), v in tune_ms.items()}}
+                     if tune_ms else {"fixed": [ctas, block, per_sm]}),
         "roofline": {"kernel": "k_batch (persistent: every pair's sample + force + solve loop)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
@@ -557,7 +640,9 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        if args.config == 3:
+        if args.config == 3 and args.single:
+            run_ours_batch_single(args, rank, world, local_rank)
+        elif args.config == 3:
             run_ours_batch(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)

@@ -143,9 +143,13 @@ typedef struct {
                           not bounded by the FP32 tolerances.  (default 0)  */
   int32_t team_ctas;   /* batched engine only: CTAs per team (one thread-block
                           cluster registers one pair at a time): 1, 2, 4 or
-                          8; 0 = 2.  block_size is the team CTAs' size there
-                          and grid_blocks the number of teams (0 = as many
-                          as are co-resident, at most one per pair).        */
+                          8; 0 = 4.  block_size is the team CTAs' size there
+                          (0 = 512) and grid_blocks the number of teams (0 =
+                          as many as are co-resident, at most one per pair). */
+  int32_t team_blocks_per_sm; /* batched engine only: CTAs per SM that the
+                          iteration kernel's register budget is sized for:
+                          1 (up to 128 registers per thread) or 2 (up to 64,
+                          the rest in local memory); 0 = 1.                 */
 } mreg_options;
 
 typedef struct {
@@ -318,17 +322,18 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
 mreg_status mreg_batch_run(mreg_batch* b, int32_t n_iters, void* stream);
 
 /* Autotuner: times mreg_batch_run(n_iters) for every supported team shape
- * (team_ctas in 1, 2, 4, 8 x block_size in 128, 256, 512, skipping shapes
- * that do not fit), keeps the fastest for later runs and returns it.  Each
- * shape is run once to warm up and timed on the best of two runs with CUDA
- * events.  times_ms (may be NULL) receives 12 entries, row-major over
- * (team_ctas, block_size), -1 for skipped shapes.  Blocks.                  */
+ * (team_ctas in 1, 2, 4, 8 x block_size in 128, 256, 512 x blocks_per_sm in
+ * 1, 2, skipping shapes that do not fit), keeps the fastest for later runs
+ * and returns it.  Each shape is run once to warm up and timed on the best
+ * of two runs with CUDA events.  times_ms (may be NULL) receives 24 entries,
+ * row-major over (team_ctas, block_size, blocks_per_sm), -1 for skipped
+ * shapes.  Blocks.  Outputs may be NULL.                                    */
 mreg_status mreg_batch_tune(mreg_batch* b, int32_t n_iters, void* stream, int32_t* team_ctas,
-                            int32_t* block_size, float* times_ms);
+                            int32_t* block_size, int32_t* blocks_per_sm, float* times_ms);
 
-/* Current team shape and number of teams. */
+/* Current team shape and number of teams (outputs may be NULL). */
 mreg_status mreg_batch_shape(mreg_batch* b, int32_t* team_ctas, int32_t* block_size,
-                             int32_t* n_teams);
+                             int32_t* blocks_per_sm, int32_t* n_teams);
 
 /* Device time of the persistent iteration kernel (with its energy sums) in
  * the last run, in ms, from CUDA events recorded around it inside the run.

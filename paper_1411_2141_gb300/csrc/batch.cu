@@ -145,8 +145,11 @@ struct ClusterTeam {
   }
 };
 
-template <int FORM, int GRAD>
-__global__ void __launch_bounds__(kIterBlockMax, 1) k_batch(const BatchArgs b) {
+// MINB: CTAs per SM the register budget is sized for (1: up to 128
+// registers per thread; 2: up to 64 for 512-thread CTAs, the rest spilled
+// to local memory).  The autotuner picks between them.
+template <int FORM, int GRAD, int MINB>
+__global__ void __launch_bounds__(kIterBlockMax, MINB) k_batch(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) IterArgs s_a;
   __shared__ int s_pos;
@@ -241,17 +244,22 @@ __global__ void k_batch_msd(const BatchWarpArgs b) {
   }
 }
 
-void* select_batch_kernel(int form, int grad) {
+template <int MINB>
+void* select_batch_kernel_m(int form, int grad) {
   switch (form * 2 + (grad ? 1 : 0)) {
-    case 0: return (void*)k_batch<kFormExplicit, 0>;
-    case 1: return (void*)k_batch<kFormExplicit, 1>;
-    case 2: return (void*)k_batch<kFormUmbrella, 0>;
-    case 3: return (void*)k_batch<kFormUmbrella, 1>;
-    case 4: return (void*)k_batch<kFormFemNodes, 0>;
-    case 5: return (void*)k_batch<kFormFemNodes, 1>;
-    case 7: return (void*)k_batch<kFormFemEdges, 1>;
+    case 0: return (void*)k_batch<kFormExplicit, 0, MINB>;
+    case 1: return (void*)k_batch<kFormExplicit, 1, MINB>;
+    case 2: return (void*)k_batch<kFormUmbrella, 0, MINB>;
+    case 3: return (void*)k_batch<kFormUmbrella, 1, MINB>;
+    case 4: return (void*)k_batch<kFormFemNodes, 0, MINB>;
+    case 5: return (void*)k_batch<kFormFemNodes, 1, MINB>;
+    case 7: return (void*)k_batch<kFormFemEdges, 1, MINB>;
     default: return nullptr;
   }
+}
+
+void* select_batch_kernel(int form, int grad, int minb) {
+  return minb == 2 ? select_batch_kernel_m<2>(form, grad) : select_batch_kernel_m<1>(form, grad);
 }
 
 int grid_for(int64_t n, int block) {
@@ -263,7 +271,7 @@ int grid_for(int64_t n, int block) {
 
 // Function attributes are set here, outside any stream capture; the
 // launchers below only enqueue work (they may be recorded into a graph).
-cudaError_t batch_prepare(int form, int grad, int block) {
+cudaError_t batch_prepare(int form, int grad, int block, int minb) {
   const size_t smem = kSmemPerWarp * kSetupWarps;
   cudaError_t e = cudaFuncSetAttribute(k_batch_prefilter<0>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -271,7 +279,7 @@ cudaError_t batch_prepare(int form, int grad, int block) {
   e = cudaFuncSetAttribute(k_batch_prefilter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
-  void* k = select_batch_kernel(form, grad);
+  void* k = select_batch_kernel(form, grad, minb);
   if (!k) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)topo_smem_bytes(block));
@@ -304,8 +312,9 @@ cudaError_t batch_count_uncovered(const BatchSetupArgs& a, const int64_t* px_off
   return cudaGetLastError();
 }
 
-cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int* max_teams) {
-  void* k = select_batch_kernel(form, grad);
+cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb,
+                            int* max_teams) {
+  void* k = select_batch_kernel(form, grad, minb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -339,9 +348,8 @@ cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int* m
 }
 
 cudaError_t batch_launch_iterate(int form, int grad, const BatchArgs& b, int n_teams, int block,
-                                 int hist_cap, cudaStream_t s) {
-  (void)hist_cap;
-  void* k = select_batch_kernel(form, grad);
+                                 int minb, cudaStream_t s) {
+  void* k = select_batch_kernel(form, grad, minb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(int), s);

@@ -24,6 +24,7 @@ namespace {
 constexpr int kBatchHist = 1024;   // per-pair history entries (energy, CG)
 constexpr int kShapesCtas[4] = {1, 2, 4, 8};
 constexpr int kShapesBlock[3] = {128, 256, 512};
+constexpr int kShapesMinb[2] = {1, 2};
 
 struct PairInfo {
   int W = 0, H = 0, nV = 0, nT = 0, nE = 0, nnz = 0;
@@ -64,7 +65,7 @@ struct mreg_batch {
   int64_t* d_px_off = nullptr;
   int* d_counts = nullptr;
   // launch shape and its scratch
-  int team_ctas = 2, block = 256, n_teams = 0;
+  int team_ctas = 2, block = 256, minb = 1, n_teams = 0;
   float* part = nullptr;     // per team reduction records
   size_t part_bytes = 0;
   float2* epart = nullptr;   // per pair energy partials
@@ -73,15 +74,16 @@ struct mreg_batch {
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_iter[2] = {nullptr, nullptr};   // around the iteration kernel
   cudaGraphExec_t exec = nullptr;
-  int exec_iters = 0, exec_ctas = 0, exec_block = 0;
+  int exec_iters = 0, exec_ctas = 0, exec_block = 0, exec_minb = 0;
   int last_n_iters = 0;
 };
 
 namespace {
 
-mreg_status choose_shape(mreg_batch* b, int ctas, int block) {
+mreg_status choose_shape(mreg_batch* b, int ctas, int block, int minb) {
   int max_teams = 0;
-  cudaError_t e = mreg::batch_max_teams(b->form, b->grad, ctas, block, &max_teams);
+  CK(mreg::batch_prepare(b->form, b->grad, block, minb), "kernel attributes");
+  cudaError_t e = mreg::batch_max_teams(b->form, b->grad, ctas, block, minb, &max_teams);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(MREG_ERR_INVALID_ARG, "team shape %d x %d threads is not supported (%s)", ctas,
@@ -92,7 +94,6 @@ mreg_status choose_shape(mreg_batch* b, int ctas, int block) {
                 block);
   int teams = std::min(max_teams, b->n_pairs);
   if (b->opts.grid_blocks > 0) teams = std::min(b->opts.grid_blocks, max_teams);
-  CK(mreg::batch_prepare(b->form, b->grad, block), "kernel attributes");
   const size_t need = (size_t)teams * 2 * ctas * mreg::kRec * sizeof(float);
   if (need > b->part_bytes) {
     if (b->exec) {   // the recorded graph points at the old buffer
@@ -107,6 +108,7 @@ mreg_status choose_shape(mreg_batch* b, int ctas, int block) {
   }
   b->team_ctas = ctas;
   b->block = block;
+  b->minb = minb;
   b->n_teams = teams;
   return MREG_OK;
 }
@@ -149,7 +151,7 @@ mreg_status enqueue_run(mreg_batch* b, int n_iters, cudaStream_t s) {
   a.epart = b->epart;
   // external records: event nodes of the graph, readable after a replay
   CK(cudaEventRecordWithFlags(b->ev_iter[0], s, cudaEventRecordExternal), "event");
-  CK(mreg::batch_launch_iterate(b->form, b->grad, a, b->n_teams, b->block, kBatchHist, s),
+  CK(mreg::batch_launch_iterate(b->form, b->grad, a, b->n_teams, b->block, b->minb, s),
      "batched iteration kernel launch");
   CK(cudaEventRecordWithFlags(b->ev_iter[1], s, cudaEventRecordExternal), "event");
   CK(mreg::batch_warp_msd(b->warp, s), "batched warp");
@@ -158,7 +160,7 @@ mreg_status enqueue_run(mreg_batch* b, int n_iters, cudaStream_t s) {
 
 mreg_status record(mreg_batch* b, int n_iters) {
   if (b->exec && b->exec_iters == n_iters && b->exec_ctas == b->team_ctas &&
-      b->exec_block == b->block)
+      b->exec_block == b->block && b->exec_minb == b->minb)
     return MREG_OK;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -184,6 +186,7 @@ mreg_status record(mreg_batch* b, int n_iters) {
   b->exec_iters = n_iters;
   b->exec_ctas = b->team_ctas;
   b->exec_block = b->block;
+  b->exec_minb = b->minb;
   return MREG_OK;
 }
 
@@ -241,6 +244,8 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   if (o.team_ctas != 0 && o.team_ctas != 1 && o.team_ctas != 2 && o.team_ctas != 4 &&
       o.team_ctas != 8)
     return fail(MREG_ERR_INVALID_ARG, "team_ctas must be 0, 1, 2, 4 or 8");
+  if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
+    return fail(MREG_ERR_INVALID_ARG, "team_blocks_per_sm must be 0, 1 or 2");
 
   // host topology of every pair
   std::vector<HostMesh> hm(n_pairs);
@@ -541,7 +546,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   wa.msd = (double*)(base + o_msd);
 
   // coverage check of every pair's pixel map
-  CK(mreg::batch_prepare(b->form, b->grad, 256), "kernel attributes");
+  CK(mreg::batch_prepare(b->form, b->grad, 256, 1), "kernel attributes");
   CK(mreg::batch_setup(sa, false, s), "batched set-up");
   CK(mreg::batch_pixel_map(sa, b->pix, b->n_px, s), "batched pixel map");
   CK(cudaMemsetAsync(b->d_counts, 0, P * 4, s), "memset");
@@ -554,7 +559,8 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
       return fail(MREG_ERR_BAD_MESH, "pair %d: %d pixel centres are not inside any triangle", p,
                   unc[p]);
 
-  st = choose_shape(b, o.team_ctas ? o.team_ctas : 2, o.block_size ? o.block_size : 256);
+  st = choose_shape(b, o.team_ctas ? o.team_ctas : 4, o.block_size ? o.block_size : 512,
+                    o.team_blocks_per_sm ? o.team_blocks_per_sm : 1);
   if (st) return st;
   guard.keep = true;
   *out = b;
@@ -573,60 +579,63 @@ mreg_status mreg_batch_run(mreg_batch* b, int32_t n_iters, void* stream) {
 }
 
 mreg_status mreg_batch_shape(mreg_batch* b, int32_t* team_ctas, int32_t* block_size,
-                             int32_t* n_teams) {
+                             int32_t* blocks_per_sm, int32_t* n_teams) {
   if (!b) return fail(MREG_ERR_INVALID_ARG, "batch is NULL");
   if (team_ctas) *team_ctas = b->team_ctas;
   if (block_size) *block_size = b->block;
+  if (blocks_per_sm) *blocks_per_sm = b->minb;
   if (n_teams) *n_teams = b->n_teams;
   return MREG_OK;
 }
 
 mreg_status mreg_batch_tune(mreg_batch* b, int32_t n_iters, void* stream, int32_t* team_ctas,
-                            int32_t* block_size, float* times_ms) {
+                            int32_t* block_size, int32_t* blocks_per_sm, float* times_ms) {
   if (!b) return fail(MREG_ERR_INVALID_ARG, "batch is NULL");
   if (n_iters < 1) return fail(MREG_ERR_INVALID_ARG, "n_iters must be >= 1");
   CK(cudaSetDevice(b->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  const int c0 = b->team_ctas, k0 = b->block;
-  int best_c = c0, best_k = k0;
+  int best_c = b->team_ctas, best_k = b->block, best_m = b->minb;
   float best = -1.0f;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
   mreg_status st = MREG_OK;
   for (int ci = 0; ci < 4 && !st; ++ci)
-    for (int ki = 0; ki < 3 && !st; ++ki) {
-      float t = -1.0f;
-      if (choose_shape(b, kShapesCtas[ci], kShapesBlock[ki]) == MREG_OK) {
-        st = mreg_batch_run(b, n_iters, stream);   // warm-up (and recording)
-        for (int r = 0; r < 2 && !st; ++r) {
-          cudaEventRecord(e0, s);
-          st = mreg_batch_run(b, n_iters, stream);
-          cudaEventRecord(e1, s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st = fail(MREG_ERR_CUDA, "autotuner run failed");
-            break;
+    for (int ki = 0; ki < 3 && !st; ++ki)
+      for (int mi = 0; mi < 2 && !st; ++mi) {
+        float t = -1.0f;
+        if (choose_shape(b, kShapesCtas[ci], kShapesBlock[ki], kShapesMinb[mi]) == MREG_OK) {
+          st = mreg_batch_run(b, n_iters, stream);   // warm-up (and recording)
+          for (int r = 0; r < 2 && !st; ++r) {
+            cudaEventRecord(e0, s);
+            st = mreg_batch_run(b, n_iters, stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+              st = fail(MREG_ERR_CUDA, "autotuner run failed");
+              break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (t < 0.0f || ms < t) t = ms;
           }
-          float ms = 0.0f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (t < 0.0f || ms < t) t = ms;
+          if (!st && t >= 0.0f && (best < 0.0f || t < best)) {
+            best = t;
+            best_c = kShapesCtas[ci];
+            best_k = kShapesBlock[ki];
+            best_m = kShapesMinb[mi];
+          }
         }
-        if (!st && t >= 0.0f && (best < 0.0f || t < best)) {
-          best = t;
-          best_c = kShapesCtas[ci];
-          best_k = kShapesBlock[ki];
-        }
+        if (times_ms) times_ms[(ci * 3 + ki) * 2 + mi] = t;
       }
-      if (times_ms) times_ms[ci * 3 + ki] = t;
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
   if (best < 0.0f) return fail(MREG_ERR_INVALID_ARG, "no team shape fits");
-  st = choose_shape(b, best_c, best_k);
+  st = choose_shape(b, best_c, best_k, best_m);
   if (st) return st;
   if (team_ctas) *team_ctas = best_c;
   if (block_size) *block_size = best_k;
+  if (blocks_per_sm) *blocks_per_sm = best_m;
   return MREG_OK;
 }
 

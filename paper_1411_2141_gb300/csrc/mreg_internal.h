@@ -169,14 +169,16 @@ struct BatchWarpArgs {
 
 constexpr int kBatchTilePx = 4096;   // pixels per warp tile
 
-cudaError_t batch_prepare(int form, int grad, int block);
+cudaError_t batch_prepare(int form, int grad, int block, int minb);
 cudaError_t batch_setup(const BatchSetupArgs& a, bool edges, cudaStream_t s);
 cudaError_t batch_pixel_map(const BatchSetupArgs& a, int* pix_all, int64_t n_px, cudaStream_t s);
 cudaError_t batch_count_uncovered(const BatchSetupArgs& a, const int64_t* px_off, int64_t n_px,
                                   const int* pix_tri, int* counts, cudaStream_t s);
-cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int* max_teams);
+// minb: the iteration kernel's register budget, sized for 1 or 2 CTAs per SM
+cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb,
+                            int* max_teams);
 cudaError_t batch_launch_iterate(int form, int grad, const BatchArgs& b, int n_teams, int block,
-                                 int hist_cap, cudaStream_t s);
+                                 int minb, cudaStream_t s);
 cudaError_t batch_warp_msd(const BatchWarpArgs& a, cudaStream_t s);
 
 }  // namespace mreg

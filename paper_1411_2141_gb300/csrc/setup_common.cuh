@@ -145,20 +145,50 @@ __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int
   }
 }
 
-__device__ __forceinline__ double orient_rn(double ax, double ay, double bx, double by, double px,
-                                            double py) {
-  const double t1 = __dmul_rn(__dsub_rn(bx, ax), __dsub_rn(py, ay));
-  const double t2 = __dmul_rn(__dsub_rn(by, ay), __dsub_rn(px, ax));
-  return __dsub_rn(t1, t2);
-}
+// Inside test of pixel centres against one edge of a triangle, written so
+// that the two triangles sharing an edge classify every point alike: the
+// orientation is always formed along the edge from its lower-numbered node
+// lo to its higher-numbered node hi,
+//   s = (Bx - Ax)(py - Ay) - (By - Ay)(px - Ax),  A = V[lo], B = V[hi],
+// in FP64 with every operation rounded separately (the differences are exact
+// in FP64 for FP32 coordinates), and the point is on the inner side when
+// s >= 0 for a triangle that runs lo -> hi along the edge, s <= 0 otherwise.
+//
+// Most pixels are far from the edge, so the sign is first taken from the
+// same expression in FP32 with Shewchuk's forward error bound (Adaptive
+// Precision Floating-Point Arithmetic and Fast Robust Geometric Predicates,
+// 1997: |s32 - s| <= (3 + 16 eps) eps (|t1| + |t2|), eps = 2^-24).  When
+// |s32| exceeds twice that bound, s is nonzero with the sign of s32 and the
+// FP64 value, whose own error is ~2^-52 (|t1| + |t2|), has the same sign, so
+// the decision is the FP64 one; otherwise the FP64 expression is evaluated.
+struct EdgeSide {
+  float ax, ay, dx, dy;          // A and B - A in FP32 (rounded)
+  double axd, ayd, dxd, dyd;     // A and B - A in FP64 (exact)
+  bool forward;                  // the triangle runs lo -> hi along this edge
 
-__device__ __forceinline__ double edge_side(const float2* __restrict__ V, int a, int b, double px,
-                                            double py) {
-  const int lo = min(a, b), hi = max(a, b);
-  const float2 A = __ldg(V + lo), B = __ldg(V + hi);
-  const double s = orient_rn(A.x, A.y, B.x, B.y, px, py);
-  return a < b ? s : -s;
-}
+  __device__ __forceinline__ void init(float2 P, float2 Q, bool fwd) {   // P = V[lo], Q = V[hi]
+    ax = P.x;
+    ay = P.y;
+    dx = __fsub_rn(Q.x, P.x);
+    dy = __fsub_rn(Q.y, P.y);
+    axd = P.x;
+    ayd = P.y;
+    dxd = __dsub_rn((double)Q.x, (double)P.x);
+    dyd = __dsub_rn((double)Q.y, (double)P.y);
+    forward = fwd;
+  }
+  __device__ __forceinline__ bool inside(int x, int y) const {
+    const float t1 = __fmul_rn(dx, __fsub_rn((float)y, ay));
+    const float t2 = __fmul_rn(dy, __fsub_rn((float)x, ax));
+    const float s = __fsub_rn(t1, t2);
+    constexpr float kBound = 2.0f * 3.0000010f * 5.9604645e-8f;   // 2 (3 + 16 eps) eps
+    if (fabsf(s) > kBound * (fabsf(t1) + fabsf(t2))) return forward ? s > 0.0f : s < 0.0f;
+    const double u1 = __dmul_rn(dxd, __dsub_rn((double)y, ayd));
+    const double u2 = __dmul_rn(dyd, __dsub_rn((double)x, axd));
+    const double sd = __dsub_rn(u1, u2);
+    return forward ? sd >= 0.0 : sd <= 0.0;
+  }
+};
 
 // Marks every pixel centre inside closed triangle t (smallest index wins).
 __device__ __forceinline__ void pixel_map_triangle(const float2* __restrict__ V,
@@ -166,19 +196,18 @@ __device__ __forceinline__ void pixel_map_triangle(const float2* __restrict__ V,
                                                    int* __restrict__ pix) {
   const int a = __ldg(tri + 3 * t), b = __ldg(tri + 3 * t + 1), c = __ldg(tri + 3 * t + 2);
   const float2 A = __ldg(V + a), B = __ldg(V + b), C = __ldg(V + c);
+  EdgeSide e[3];
+  e[0].init(a < b ? A : B, a < b ? B : A, a < b);
+  e[1].init(b < c ? B : C, b < c ? C : B, b < c);
+  e[2].init(c < a ? C : A, c < a ? A : C, c < a);
   const int x0 = max(0, (int)ceilf(fminf(A.x, fminf(B.x, C.x))));
   const int x1 = min(W - 1, (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x))));
   const int y0 = max(0, (int)ceilf(fminf(A.y, fminf(B.y, C.y))));
   const int y1 = min(H - 1, (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y))));
-  for (int y = y0; y <= y1; ++y) {
-    const double py = (double)y;
-    for (int x = x0; x <= x1; ++x) {
-      const double px = (double)x;
-      if (edge_side(V, a, b, px, py) >= 0.0 && edge_side(V, b, c, px, py) >= 0.0 &&
-          edge_side(V, c, a, px, py) >= 0.0)
+  for (int y = y0; y <= y1; ++y)
+    for (int x = x0; x <= x1; ++x)
+      if (e[0].inside(x, y) && e[1].inside(x, y) && e[2].inside(x, y))
         atomicMin(pix + (int64_t)y * W + x, t);
-    }
-  }
 }
 
 // Registered value R = Te(x + u(x)) at pixel p and its difference with Re

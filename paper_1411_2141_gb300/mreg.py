@@ -76,7 +76,8 @@ class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
-                ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32)]
+                ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
+                ("team_blocks_per_sm", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -137,9 +138,10 @@ def load(path: str | None = None) -> C.CDLL:
                                C.POINTER(mreg_image), dbl, dbl, C.POINTER(mreg_options), vp,
                                C.POINTER(vp)], i32),
         "mreg_batch_run": ([vp, i32, vp], i32),
-        "mreg_batch_tune": ([vp, i32, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)],
-                            i32),
-        "mreg_batch_shape": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
+        "mreg_batch_tune": ([vp, i32, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                             C.POINTER(C.c_float)], i32),
+        "mreg_batch_shape": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                              C.POINTER(i32)], i32),
         "mreg_batch_iterate_ms": ([vp, C.POINTER(C.c_float)], i32),
         "mreg_batch_msd": ([vp, C.POINTER(dbl), vp], i32),
         "mreg_batch_get_field": ([vp, i32, i32, vp, i32, C.POINTER(i64), vp], i32),
@@ -199,7 +201,7 @@ def default_options() -> mreg_options:
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
-                 coeff_bf16=False, team_ctas=0) -> mreg_options:
+                 coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -215,6 +217,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     o.coeff_bf16 = int(bool(coeff_bf16))
     o.team_ctas = int(team_ctas)
+    o.team_blocks_per_sm = int(team_blocks_per_sm)
     return o
 
 
@@ -423,24 +426,27 @@ class Batch:
         _check(load().mreg_batch_run(self._h, int(n_iters), _stream_ptr(stream)), "mreg_batch_run")
 
     def tune(self, n_iters: int, stream=None):
-        """Autotune the team shape; returns (team_ctas, block_size, times)
-        with times[(ctas, block)] in ms (None where the shape is skipped)."""
-        c, k = C.c_int32(), C.c_int32()
-        t = (C.c_float * 12)()
+        """Autotune the team shape; returns ((team_ctas, block_size,
+        blocks_per_sm), times) with times[(ctas, block, per_sm)] in ms (None
+        where the shape is skipped)."""
+        c, k, m = C.c_int32(), C.c_int32(), C.c_int32()
+        t = (C.c_float * 24)()
         _check(load().mreg_batch_tune(self._h, int(n_iters), _stream_ptr(stream), C.byref(c),
-                                      C.byref(k), t), "mreg_batch_tune")
+                                      C.byref(k), C.byref(m), t), "mreg_batch_tune")
         times = {}
         for i, ctas in enumerate((1, 2, 4, 8)):
             for j, blk in enumerate((128, 256, 512)):
-                v = float(t[i * 3 + j])
-                times[(ctas, blk)] = v if v >= 0 else None
-        return c.value, k.value, times
+                for q, per_sm in enumerate((1, 2)):
+                    v = float(t[(i * 3 + j) * 2 + q])
+                    times[(ctas, blk, per_sm)] = v if v >= 0 else None
+        return (c.value, k.value, m.value), times
 
     def shape(self):
-        c, k, n = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(load().mreg_batch_shape(self._h, C.byref(c), C.byref(k), C.byref(n)),
+        """(team_ctas, block_size, blocks_per_sm, n_teams)."""
+        c, k, m, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().mreg_batch_shape(self._h, C.byref(c), C.byref(k), C.byref(m), C.byref(n)),
                "mreg_batch_shape")
-        return c.value, k.value, n.value
+        return c.value, k.value, m.value, n.value
 
     def iterate_ms(self) -> float:
         """Device time of the iteration kernel in the last run (ms)."""

@@ -132,15 +132,31 @@ def test_pair_result_does_not_depend_on_the_batch(mreg, small):
 def test_autotuner_picks_a_timed_shape(mreg, small, oracle_small):
     n = 30
     with _batch(mreg, small, mode="S1") as b:
-        ctas, block, times = b.tune(n)
+        best, times = b.tune(n)
         timed = {k: v for k, v in times.items() if v is not None}
-        assert (ctas, block) in timed and timed[(ctas, block)] == min(timed.values())
-        assert b.shape()[:2] == (ctas, block)
+        assert best in timed and timed[best] == min(timed.values())
+        assert b.shape()[:3] == best
         b.run(n)
         for k in (0, 1):
             u_ref, _, msd_ref = oracle_small(k, "S1", "G0", "Q0", n)
             assert np.abs(b.get_u(k) - u_ref).max() <= U_TOL
             assert abs(b.msd()[k] - msd_ref) / msd_ref <= MSD_RTOL
+
+
+@pytest.mark.parametrize("mode,grad", [("S1", "G0"), ("S2", "G1")])
+def test_two_ctas_per_sm_register_budget(mreg, small, oracle_small, mode, grad):
+    """The 64-register variant of the iteration kernel (spills to local
+    memory) gives the oracle's results too."""
+    n = 30
+    with _batch(mreg, small, mode=mode, grad=grad, team_ctas=2, block_size=256,
+                team_blocks_per_sm=2) as b:
+        assert b.shape()[:3] == (2, 256, 2)
+        b.run(n)
+        msd = b.msd()
+        for k in range(len(small)):
+            u_ref, _, msd_ref = oracle_small(k, mode, grad, "Q0", n)
+            assert np.abs(b.get_u(k) - u_ref).max() <= U_TOL
+            assert abs(msd[k] - msd_ref) / msd_ref <= MSD_RTOL
 
 
 def test_fields_of_a_pair(mreg, small):
