@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--team", default=None,
                    help="config 3: fixed team shape 'ctas,block[,blocks_per_sm]' instead of "
                         "the autotuner")
+    p.add_argument("--pairs", type=int, default=0,
+                   help="config 3: only the first N pairs of the batch (small profiling case)")
     p.add_argument("--single", action="store_true",
                    help="config 3: register the pairs one after another with the one-pair "
                         "engine (the plain FP32 form) instead of the batched engine")
@@ -191,7 +193,7 @@ def launches_per_registration(args, n_iter: int) -> int:
 
 
 def run_reference_batch(args):
-    cases = batch_cases()
+    cases = batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     for _ in range(args.warmup):
         oracle_registration_time(cases[0], args.mode, args.grad, sample_iters=2)
@@ -244,6 +246,35 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     """Units of all ranks per second of the slowest rank (weak scaling)."""
     return units_per_rank * world / seconds
+
+
+PROFILE_C1 = ("k_implicit_512px_20k_nodes.md",
+              ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "iterate.cu",
+               "mreg_internal.h"])
+PROFILE_C3 = ("k_batch_256_uneven_pairs.md",
+              ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "batch.cu",
+               "setup_common.cuh", "mreg_internal.h"])
+
+
+def profiled_traffic(profile):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's sources changed since the capture (or no full-size capture)."""
+    import hashlib
+    import re
+    name, sources = profile
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"source sha256 \([^)]*\): ([0-9a-f]+)", text)
+    m_bytes = re.search(r"DRAM bytes per launch: (\d+)", text)
+    if not (m_hash and m_bytes):
+        return None
+    h = hashlib.sha256()
+    for f in sources:
+        with open(os.path.join(ROOT, "paper_1411_2141_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return int(m_bytes.group(1)) if h.hexdigest()[:len(m_hash.group(1))] == m_hash.group(1) else None
 
 
 def peak_hbm():
@@ -370,7 +401,9 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak,
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": per_iter * n_iter,
-                     "traffic": None},
+                     "traffic": (profiled_traffic(PROFILE_C1)
+                                 if (args.config, args.mode, args.grad, args.coeff)
+                                 == (1, "S1", "G0", "fp32") else None)},
         "clocks": clk,
         "gpu_launches": launches_per_registration(args, n_iter) * args.steps,
         "launch": {"grid": st["grid_blocks"], "block": st["block_size"]},
@@ -410,8 +443,8 @@ def batch_workload_config(args, cases, shape=None):
     return cfg
 
 
-def batch_cases():
-    return inputs.make_cases(inputs.batched_specs(3))
+def batch_cases(n_pairs: int = 0):
+    return inputs.make_cases(inputs.batched_specs(3, n_pairs or None))
 
 
 def oracle_batch_time(cases, mode: str, grad: str, n_sample_pairs: int = 8, sample_iters: int = 10):
@@ -437,7 +470,7 @@ def run_ours_batch_single(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     mreg.load()
-    cases = batch_cases()
+    cases = batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
     regs = [mreg.Registration(c.V, c.T, torch.from_numpy(c.Re).to(dev),
@@ -499,7 +532,7 @@ def run_ours_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     mreg.load()
-    cases = batch_cases()
+    cases = batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
     bf16 = args.coeff == "bf16"
@@ -610,7 +643,8 @@ def run_ours_batch(args, rank, world, local_rank):
         "roofline": {"kernel": "k_batch (persistent: every pair's sample + force + solve loop)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": per_iter_total * n_iter, "traffic": None},
+                     "algorithmic_bytes_per_launch": per_iter_total * n_iter,
+                     "traffic": profiled_traffic(PROFILE_C3) if not args.pairs else None},
         "clocks": clk,
         "gpu_launches": BATCH_LAUNCHES * args.steps,
     }
