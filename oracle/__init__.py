@@ -13,6 +13,8 @@ Modules
             operator, P1 mass / stiffness matrices
   register  Algorithm 1 (setup, sampling, force, update / solve, energy),
             dense warp and MSD
+  adjoint   the warp-plus-SSD energy of a node displacement and its exact
+            gradient with respect to the node displacements
 
 Parity status
   Every function here is pinned by a ``-m "not gpu"`` test against a fact

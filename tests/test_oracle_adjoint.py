@@ -1,0 +1,76 @@
+"""Pins of the oracle's warp energy and its gradient (oracle/adjoint.py).
+
+  * FP64 central differences (h = 1e-6) of E reproduce the analytic gradient
+    (a wrong lambda, a missing chain-rule factor, a sign or a swapped x/y all
+    fail this);
+  * identical images at u = 0 give E = 0 and a zero gradient;
+  * summed over nodes the gradient equals the dense sum of r grad Te, since
+    the barycentric coordinates of a pixel sum to 1;
+  * E equals HW/2 times the MSD that register.Problem reports.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint, bspline, register
+from paper_1411_2141_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    spec = inputs.CaseSpec(side=48, n_nodes=120, seed=11, n_blobs=8, dmax=2.0, n_iter=5)
+    return inputs.make_case(spec)
+
+
+def _problem(c):
+    return register.Problem(c.V, c.T, c.Re, c.Te, 0.1, 1.0, "S0", "G1")
+
+
+def _smooth_u(c, amp=0.7, seed=3):
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(0.5, 1.5, size=4)
+    x, y = c.V[:, 0].astype(np.float64), c.V[:, 1].astype(np.float64)
+    s = c.spec.side
+    return amp * np.stack([np.sin(2 * np.pi * k[0] * x / s + k[1]),
+                           np.cos(2 * np.pi * k[2] * y / s + k[3])], axis=1)
+
+
+def test_gradient_matches_central_differences(small_case):
+    pb = _problem(small_case)
+    u = _smooth_u(small_case)
+    _, g = adjoint.warp_energy_grad(pb, u)
+    rng = np.random.default_rng(0)
+    h = 1e-6
+    for a in rng.choice(pb.n, size=12, replace=False):
+        for c in range(2):
+            up = u.copy()
+            um = u.copy()
+            up[a, c] += h
+            um[a, c] -= h
+            fd = (adjoint.warp_energy(pb, up) - adjoint.warp_energy(pb, um)) / (2 * h)
+            assert abs(fd - g[a, c]) <= 1e-6 * max(1.0, np.abs(g).max()), (a, c, fd, g[a, c])
+
+
+def test_identical_images_give_zero(small_case):
+    c = small_case
+    pb = register.Problem(c.V, c.T, c.Re, c.Re, 0.1, 1.0, "S0", "G1")
+    E, g = adjoint.warp_energy_grad(pb, np.zeros((pb.n, 2)))
+    assert E < 1e-20 and np.abs(g).max() < 1e-10
+
+
+def test_gradient_sum_is_dense_sum(small_case):
+    pb = _problem(small_case)
+    u = _smooth_u(small_case)
+    _, g = adjoint.warp_energy_grad(pb, u)
+    ud = pb.dense_displacement(u)
+    ys, xs = np.mgrid[0:pb.H, 0:pb.W].astype(np.float64)
+    val, gx, gy = bspline.evaluate(pb.cTe, xs + ud[..., 0], ys + ud[..., 1], grad=True)
+    r = val - pb.Re
+    np.testing.assert_allclose(g.sum(axis=0), [np.sum(r * gx), np.sum(r * gy)], rtol=1e-10,
+                               atol=1e-10)
+
+
+def test_energy_is_half_the_pixel_sum_of_the_msd(small_case):
+    pb = _problem(small_case)
+    u = _smooth_u(small_case)
+    E, _ = adjoint.warp_energy_grad(pb, u)
+    assert E == pytest.approx(0.5 * pb.H * pb.W * pb.msd(u), rel=1e-12)
