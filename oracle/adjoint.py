@@ -18,10 +18,20 @@ linear interpolation (d u(x) / d u_a = lambda_a(x)):
 where star(a) are the pixels owned by the triangles around a and grad Te is
 the analytic derivative of the cubic B-spline.
 
-Pinned by ``tests/test_oracle_adjoint.py``: FP64 central differences of E,
-zero gradient on identical images, the sum over nodes equal to the dense sum
-of r grad Te (the lambdas of a pixel sum to 1), and the energy equal to
-HW/2 times the MSD of ``register.Problem``.
+Unrolled iterations.  For the explicit form with the spline gradient (S0,
+G1: Algorithm 1 with F_a = r_a grad Te(V_a + u_a)), one iteration is
+u' = S (u - tau F(u)) with S = (1 - l) I + l A^Lap (Eq. 5, 14), so its
+Jacobian is S (I - tau D) with the 2x2 block of every node
+
+    D_a = dF_a/du_a = grad Te grad Te^T + r_a Hess Te     (at V_a + u_a),
+
+and the gradient of E(u_K) with respect to the starting u_0 is the adjoint
+recursion v_K = dE/du_K, v_k = (I - tau D(u_k)) S^T v_{k+1}, returned as v_0.
+
+Pinned by ``tests/test_oracle_adjoint.py``: FP64 central differences of E
+and of E(u_K(u_0)), zero gradient on identical images, the sum over nodes
+equal to the dense sum of r grad Te (the lambdas of a pixel sum to 1), and
+the energy equal to HW/2 times the MSD of ``register.Problem``.
 """
 from __future__ import annotations
 
@@ -68,3 +78,36 @@ def warp_energy_grad(pb, u):
         np.add.at(g[:, 0], corners[:, k], lam[:, k] * r * gx)
         np.add.at(g[:, 1], corners[:, k], lam[:, k] * r * gy)
     return 0.5 * float(np.sum(r * r)), g
+
+
+def unrolled_energy(pb, u0, n_iter: int) -> float:
+    """E(u_K) after n_iter iterations of pb (S0, G1) from u_0."""
+    u, _ = pb.run(n_iter, u0)
+    return warp_energy(pb, u)
+
+
+def unrolled_grad(pb, u0, n_iter: int):
+    """(E(u_K), dE(u_K)/du_0) through n_iter iterations of pb (S0, G1)."""
+    if pb.mode != "S0" or pb.grad != "G1":
+        raise ValueError("the unrolled gradient is defined for the explicit form with the "
+                         "spline gradient")
+    u = np.asarray(u0, dtype=np.float64).copy()
+    states = []
+    for _ in range(n_iter):
+        states.append(u)
+        u, _ = pb.step(u)
+    E, v = warp_energy_grad(pb, u)
+    AlapT = pb.Alap.T.tocsr()
+    for uk in reversed(states):
+        w = (1.0 - pb.lam) * v + pb.lam * (AlapT @ v)        # S^T v
+        P = pb.V + uk
+        f, gx, gy = bspline.evaluate(pb.cTe, P[:, 0], P[:, 1], grad=True)
+        hxx, hxy, hyy = bspline.hessian(pb.cTe, P[:, 0], P[:, 1])
+        r = f - pb.ReV
+        d00 = gx * gx + r * hxx
+        d01 = gx * gy + r * hxy
+        d11 = gy * gy + r * hyy
+        v = np.stack([w[:, 0] - pb.tau * (d00 * w[:, 0] + d01 * w[:, 1]),
+                      w[:, 1] - pb.tau * (d01 * w[:, 0] + d11 * w[:, 1])], axis=1)
+    return E, v
+

@@ -87,6 +87,39 @@ def cubic_dweights(t: np.ndarray):
     return (d0, d1, d2, d3)
 
 
+def cubic_d2weights(t: np.ndarray):
+    """Second derivatives of :func:`cubic_weights` with respect to t."""
+    return (1.0 - t, 3.0 * t - 2.0, 1.0 - 3.0 * t, t + 0.0 * t)
+
+
+def hessian(coef: np.ndarray, x, y):
+    """Second derivatives (d2/dx2, d2/dxdy, d2/dy2) of the spline at (x, y),
+    FP64, with the same mirror extension as :func:`evaluate`."""
+    coef = np.asarray(coef, dtype=np.float64)
+    H, W = coef.shape
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    ix = np.floor(x)
+    iy = np.floor(y)
+    tx, ty = x - ix, y - iy
+    ix = ix.astype(np.int64)
+    iy = iy.astype(np.int64)
+    wx, wy = cubic_weights(tx), cubic_weights(ty)
+    dx, dy = cubic_dweights(tx), cubic_dweights(ty)
+    ex, ey = cubic_d2weights(tx), cubic_d2weights(ty)
+    hxx = np.zeros(np.broadcast(x, y).shape)
+    hxy = np.zeros_like(hxx)
+    hyy = np.zeros_like(hxx)
+    for m in range(4):
+        rows = mirror_index(iy - 1 + m, H)
+        for n in range(4):
+            c = coef[rows, mirror_index(ix - 1 + n, W)]
+            hxx += wy[m] * ex[n] * c
+            hxy += dy[m] * dx[n] * c
+            hyy += ey[m] * wx[n] * c
+    return hxx, hxy, hyy
+
+
 def evaluate(coef: np.ndarray, x, y, grad: bool = False):
     """Spline value (and optionally d/dx, d/dy) at points (x, y), FP64.
 

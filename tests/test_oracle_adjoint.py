@@ -6,7 +6,11 @@
   * identical images at u = 0 give E = 0 and a zero gradient;
   * summed over nodes the gradient equals the dense sum of r grad Te, since
     the barycentric coordinates of a pixel sum to 1;
-  * E equals HW/2 times the MSD that register.Problem reports.
+  * E equals HW/2 times the MSD that register.Problem reports;
+  * the spline Hessian matches central differences of the spline gradient;
+  * the unrolled gradient dE(u_K)/du_0 matches central differences of the
+    composed FP64 function (a dropped Hessian term, a transposed S or a
+    wrong tau all fail it).
 """
 import numpy as np
 import pytest
@@ -74,3 +78,51 @@ def test_energy_is_half_the_pixel_sum_of_the_msd(small_case):
     u = _smooth_u(small_case)
     E, _ = adjoint.warp_energy_grad(pb, u)
     assert E == pytest.approx(0.5 * pb.H * pb.W * pb.msd(u), rel=1e-12)
+
+
+def test_spline_hessian_matches_differences_of_the_gradient(small_case):
+    pb = _problem(small_case)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-3, pb.W + 2, 40)
+    y = rng.uniform(-3, pb.H + 2, 40)
+    hxx, hxy, hyy = bspline.hessian(pb.cTe, x, y)
+    h = 1e-5
+    _, gxp, gyp = bspline.evaluate(pb.cTe, x + h, y, grad=True)
+    _, gxm, gym = bspline.evaluate(pb.cTe, x - h, y, grad=True)
+    _, gxq, _ = bspline.evaluate(pb.cTe, x, y + h, grad=True)
+    _, gxr, _ = bspline.evaluate(pb.cTe, x, y - h, grad=True)
+    _, _, gyq = bspline.evaluate(pb.cTe, x, y + h, grad=True)
+    _, _, gyr = bspline.evaluate(pb.cTe, x, y - h, grad=True)
+    # away from cell boundaries the second derivative is smooth
+    ok = (np.abs(x - np.round(x)) > 2 * h) & (np.abs(y - np.round(y)) > 2 * h)
+    sc = max(1.0, np.abs(hxx).max())
+    np.testing.assert_allclose(hxx[ok], ((gxp - gxm) / (2 * h))[ok], atol=1e-6 * sc)
+    np.testing.assert_allclose(hxy[ok], ((gyp - gym) / (2 * h))[ok], atol=1e-6 * sc)
+    np.testing.assert_allclose(hxy[ok], ((gxq - gxr) / (2 * h))[ok], atol=1e-6 * sc)
+    np.testing.assert_allclose(hyy[ok], ((gyq - gyr) / (2 * h))[ok], atol=1e-6 * sc)
+
+
+def test_unrolled_gradient_matches_central_differences(small_case):
+    pb = _problem(small_case)
+    u0 = _smooth_u(small_case, amp=0.5, seed=9)
+    K = 5
+    _, g = adjoint.unrolled_grad(pb, u0, K)
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    scale = max(1.0, np.abs(g).max())
+    for a in rng.choice(pb.n, size=8, replace=False):
+        for c in range(2):
+            up = u0.copy()
+            um = u0.copy()
+            up[a, c] += h
+            um[a, c] -= h
+            fd = (adjoint.unrolled_energy(pb, up, K) - adjoint.unrolled_energy(pb, um, K)) / (2 * h)
+            assert abs(fd - g[a, c]) <= 1e-6 * scale, (a, c, fd, g[a, c])
+
+
+def test_unrolled_gradient_of_zero_iterations_is_the_warp_gradient(small_case):
+    pb = _problem(small_case)
+    u0 = _smooth_u(small_case, amp=0.5, seed=9)
+    E0, g0 = adjoint.unrolled_grad(pb, u0, 0)
+    E1, g1 = adjoint.warp_energy_grad(pb, u0)
+    assert E0 == E1 and np.array_equal(g0, g1)
