@@ -228,6 +228,41 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream);
  *   msd_dev  device double for MSD = mean over pixels of (R - Re)^2, or NULL. */
 mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* stream);
 
+/* Warp energy and its adjoint (the differentiation form of step a4).
+ * For an arbitrary node displacement u (not the handle's own):
+ *   E(u) = 1/2 sum_x (Te(x + u(x)) - Re(x))^2,  u(x) = P1 interpolation of u
+ *          on the undeformed mesh (Sec. 1, Fig. 3; the pixel SSD of Table 1),
+ *   dE/du_a = sum_{x owned by a triangle at a} lambda_a(x) r(x) grad Te(x + u(x)),
+ *          r = Te(x + u(x)) - Re(x), grad Te the analytic B-spline derivative.
+ *   u_dev       device n_nodes x 2 float (x, y per node)
+ *   energy_dev  device double for E, or NULL
+ *   grad_dev    device n_nodes x 2 float for dE/du, or NULL
+ * The sums run in a fixed order (pixels -> per-triangle corner partials in
+ * row-major pixel order -> per-node sums over the incident triangles in
+ * ascending order): results are bitwise repeatable.  The first call
+ * allocates 8 bytes per pixel + 24 per triangle of scratch.  Asynchronous.  */
+mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* energy_dev,
+                                  float* grad_dev, void* stream);
+
+/* Gradient of the warp energy through unrolled iterations: runs n_iters
+ * iterations of the handle's loop from u0 (explicit mode S0 with the spline
+ * gradient only), evaluates E(u_K) as in mreg_warp_energy_grad, and returns
+ * dE(u_K)/du0 by the adjoint recursion
+ *   v_K = dE/du_K,   v_k = (I - tau D(u_k)) S^T v_{k+1},
+ *   S = (1 - l) I + l A^Lap (Eq. 5, 14),  D_a = grad Te grad Te^T + r_a Hess Te
+ * (the Jacobian of the force of Eq. 6 with the B-spline gradient, evaluated at
+ * V_a + u_k,a).  Every state u_0 .. u_{K-1} is kept on the device (8 bytes per
+ * node and iteration).
+ *   u0_dev      device n_nodes x 2 float
+ *   energy_dev  device double for E(u_K), or NULL
+ *   grad_dev    device n_nodes x 2 float for dE/du0, or NULL
+ * The handle's iterate is left at u_K (as after mreg_set_u(u0) and
+ * mreg_step(n_iters)).  INVALID_ARG for another mode or gradient.
+ * Asynchronous (a first call, or a larger n_iters, synchronises the stream
+ * once to grow the state buffer).                                          */
+mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
+                             double* energy_dev, float* grad_dev, void* stream);
+
 /* MSD of the current displacement (abstract; Table 1), FP64.  Blocks until
  * the value is on the host.                                                 */
 mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream);

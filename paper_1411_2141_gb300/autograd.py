@@ -1,0 +1,71 @@
+"""``torch.autograd.Function`` wrappers of the library's adjoint kernels.
+
+Argument marshalling only: the energy and its gradient are computed by
+``mreg_warp_energy_grad`` in libmreg (see include/mreg.h); PyTorch supplies
+the device tensors, the stream and the autograd graph.
+
+    E = warp_energy(u, reg)      # E(u) = 1/2 sum_x (Te(x + u(x)) - Re(x))^2
+    E.backward()                 # u.grad = dE/du  (n_nodes x 2)
+
+    E = unrolled_warp_energy(u0, reg, 20)   # E(u_20), u_20 = 20 iterations from u0
+    E.backward()                            # u0.grad = dE(u_20)/du0
+"""
+from __future__ import annotations
+
+import torch
+
+from . import mreg as _mreg
+
+__all__ = ["WarpEnergy", "warp_energy", "UnrolledWarpEnergy", "unrolled_warp_energy"]
+
+
+class WarpEnergy(torch.autograd.Function):
+    """E(u) of a registration handle's images and mesh, FP64 scalar; its
+    gradient with respect to u (FP32) is formed in the same call and kept
+    for the backward pass."""
+
+    @staticmethod
+    def forward(ctx, u: torch.Tensor, reg: "_mreg.Registration") -> torch.Tensor:
+        uc = u.detach().to(torch.float32).contiguous()
+        energy = torch.empty(1, dtype=torch.float64, device=u.device)
+        grad = torch.empty_like(uc) if ctx.needs_input_grad[0] else None
+        reg.warp_energy_grad(uc, energy, grad)
+        ctx.save_for_backward(grad)
+        return energy.reshape(())
+
+    @staticmethod
+    def backward(ctx, g_energy: torch.Tensor):
+        (grad,) = ctx.saved_tensors
+        if grad is None:
+            return None, None
+        return (grad * g_energy.to(grad.dtype)), None
+
+
+def warp_energy(u: torch.Tensor, reg: "_mreg.Registration") -> torch.Tensor:
+    return WarpEnergy.apply(u, reg)
+
+
+class UnrolledWarpEnergy(torch.autograd.Function):
+    """E(u_K) with u_K = K explicit iterations (spline gradient) of the
+    handle's loop from u0; its gradient with respect to u0 comes from the
+    library's adjoint recursion over the kept states."""
+
+    @staticmethod
+    def forward(ctx, u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int) -> torch.Tensor:
+        uc = u0.detach().to(torch.float32).contiguous()
+        energy = torch.empty(1, dtype=torch.float64, device=u0.device)
+        grad = torch.empty_like(uc) if ctx.needs_input_grad[0] else None
+        reg.unroll_grad(uc, n_iters, energy, grad)
+        ctx.save_for_backward(grad)
+        return energy.reshape(())
+
+    @staticmethod
+    def backward(ctx, g_energy: torch.Tensor):
+        (grad,) = ctx.saved_tensors
+        if grad is None:
+            return None, None, None
+        return (grad * g_energy.to(grad.dtype)), None, None
+
+
+def unrolled_warp_energy(u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int) -> torch.Tensor:
+    return UnrolledWarpEnergy.apply(u0, reg, n_iters)

@@ -249,6 +249,10 @@ struct mreg_handle {
   float2* V = nullptr;
   int *tri = nullptr, *inc_ptr = nullptr;
   int2* inc_opp = nullptr;
+  int* inc_tri = nullptr;      // incident triangle ids (same order as inc_opp)
+  void* adj_buf = nullptr;     // warp-energy adjoint scratch, allocated on first use
+  void* unroll_buf = nullptr;  // unrolled-adjoint states and vectors, grown on demand
+  size_t unroll_bytes = 0;
   int *adj_ptr = nullptr, *adj_col = nullptr, *adj_edge = nullptr;
   int2* edges = nullptr;
   float *edge_w = nullptr, *lumped = nullptr, *Mdiag = nullptr, *Moff = nullptr, *Adiag = nullptr,
@@ -571,7 +575,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   const size_t o_Re = take(npx * 4), o_Te = take(npx * 4), o_cRe = take(npx * 4),
                o_cTe = take(npx * 4), o_tmp = take(npx * 4), o_pix = take(npx * 4),
                o_V = take(nV * 8), o_tri = take(nT * 12), o_incp = take((nV + 1) * 4),
-               o_inct = take(nT * 24), o_adjp = take((nV + 1) * 4), o_adjc = take(nnz * 4),
+               o_inct = take(nT * 24), o_incid = take(nT * 12), o_adjp = take((nV + 1) * 4), o_adjc = take(nnz * 4),
                o_adje = take(nnz * 4), o_edges = take(nE * 8), o_ew = take(nE * 4),
                o_lump = take(nV * 4), o_Md = take(nV * 4), o_Mo = take(nnz * 4),
                o_Ad = take(nV * 4), o_Ao = take(nnz * 4), o_dinv = take(nV * 4),
@@ -596,6 +600,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->tri = (int*)(base + o_tri);
   h->inc_ptr = (int*)(base + o_incp);
   h->inc_opp = (int2*)(base + o_inct);
+  h->inc_tri = (int*)(base + o_incid);
   h->adj_ptr = (int*)(base + o_adjp);
   h->adj_col = (int*)(base + o_adjc);
   h->adj_edge = (int*)(base + o_adje);
@@ -641,6 +646,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   CK(up(h->tri, hm.tri.data(), nT * 12), "upload");
   CK(up(h->inc_ptr, hm.inc_ptr.data(), (nV + 1) * 4), "upload");
   CK(up(h->inc_opp, hm.inc_opp.data(), nT * 24), "upload");
+  CK(up(h->inc_tri, hm.inc_tri.data(), nT * 12), "upload");
   CK(up(h->adj_ptr, hm.adj_ptr.data(), (nV + 1) * 4), "upload");
   CK(up(h->adj_col, hm.adj_col.data(), (size_t)hm.nnz * 4), "upload");
   CK(up(h->adj_edge, hm.adj_edge.data(), (size_t)hm.nnz * 4), "upload");
@@ -686,6 +692,89 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
   }
   h->iterations_done += n_iters;
   h->last_n_iters = n_iters;
+  return MREG_OK;
+}
+
+mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* energy_dev,
+                                  float* grad_dev, void* stream) {
+  if (!h || !u_dev) return fail(MREG_ERR_INVALID_ARG, "handle or u is NULL");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  if (!energy_dev && !grad_dev) return MREG_OK;
+  const size_t rg_bytes = align_up((size_t)h->W * h->H * sizeof(float2));
+  if (!h->adj_buf)
+    CK(cudaMalloc(&h->adj_buf, rg_bytes + 3 * (size_t)h->nT * sizeof(float2)), "device allocation");
+  mreg::WarpArgs a{};
+  a.W = h->W;
+  a.H = h->H;
+  a.nT = h->nT;
+  a.V = h->V;
+  a.tri = h->tri;
+  a.pix_tri = h->pix_tri;
+  a.u = (const float2*)u_dev;
+  a.cTe = h->cTe;
+  a.cTe16 = h->cTe16;
+  a.Re = h->Re;
+  a.part = h->warp_part;
+  float2* rg = (float2*)h->adj_buf;
+  float2* tpart = (float2*)((char*)h->adj_buf + rg_bytes);
+  CK(mreg::launch_warp_grad(a, h->warp_grid, rg, tpart, h->inc_ptr, h->inc_tri, h->nV, energy_dev,
+                            (float2*)grad_dev, (cudaStream_t)stream),
+     "warp adjoint launch");
+  return MREG_OK;
+}
+
+mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
+                             double* energy_dev, float* grad_dev, void* stream) {
+  if (!h || !u0_dev) return fail(MREG_ERR_INVALID_ARG, "handle or u0 is NULL");
+  if (h->form != mreg::kFormExplicit || h->grad != MREG_GRAD_SPLINE)
+    return fail(MREG_ERR_INVALID_ARG,
+                "the unrolled gradient needs the explicit mode with the spline gradient");
+  if (n_iters < 0 || n_iters > 100000) return fail(MREG_ERR_INVALID_ARG, "n_iters out of range");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vec = align_up(sizeof(float2) * h->nV);
+  const size_t need = vec * ((size_t)n_iters + 2);
+  if (need > h->unroll_bytes) {
+    CK(cudaStreamSynchronize(s), "synchronize");
+    if (h->unroll_buf) cudaFree(h->unroll_buf);
+    h->unroll_buf = nullptr;
+    h->unroll_bytes = 0;
+    CK(cudaMalloc(&h->unroll_buf, need), "device allocation");
+    h->unroll_bytes = need;
+  }
+  char* base = (char*)h->unroll_buf;
+  float2* va = (float2*)(base + vec * n_iters);
+  float2* vb = (float2*)(base + vec * (n_iters + 1));
+  // forward: u_0 .. u_{K-1} kept, the handle's iteration runs one step at a time
+  CK(cudaMemcpyAsync(h->u, u0_dev, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s), "copy u0");
+  for (int k = 0; k < n_iters; ++k) {
+    CK(cudaMemcpyAsync(base + vec * k, h->u, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s),
+       "copy state");
+    mreg_status st = mreg_step(h, 1, stream);
+    if (st) return st;
+  }
+  mreg_status st = mreg_warp_energy_grad(h, (const float*)h->u, energy_dev,
+                                         grad_dev ? (float*)va : nullptr, stream);
+  if (st || !grad_dev) return st;
+  mreg::UnrollArgs a{};
+  a.nV = h->nV;
+  a.W = h->W;
+  a.H = h->H;
+  a.tau = (float)h->tau;
+  a.lam = (float)h->lam;
+  a.V = h->V;
+  a.adj_ptr = h->adj_ptr;
+  a.adj_col = h->adj_col;
+  a.cTe = h->cTe;
+  a.cTe16 = h->cTe16;
+  a.ReV = h->ReV;
+  for (int k = n_iters - 1; k >= 0; --k) {
+    CK(mreg::launch_unroll_adjoint_step(a, (const float2*)(base + vec * k), va, vb, s),
+       "adjoint step launch");
+    std::swap(va, vb);
+  }
+  CK(cudaMemcpyAsync(grad_dev, va, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s),
+     "copy gradient");
   return MREG_OK;
 }
 
@@ -820,9 +909,11 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
 
 void mreg_destroy(mreg_handle* h) {
   if (!h) return;
-  if (h->arena) {
+  if (h->arena || h->adj_buf || h->unroll_buf) {
     cudaSetDevice(h->dev);
-    cudaFree(h->arena);
+    if (h->arena) cudaFree(h->arena);
+    if (h->adj_buf) cudaFree(h->adj_buf);
+    if (h->unroll_buf) cudaFree(h->unroll_buf);
   }
   delete h;
 }

@@ -44,6 +44,14 @@ __device__ __forceinline__ void cubic_dweights(float t, float d[4]) {
   d[3] = 0.5f * t2;
 }
 
+// d2/dt2 of cubic_weights.
+__device__ __forceinline__ void cubic_d2weights(float t, float e[4]) {
+  e[0] = 1.0f - t;
+  e[1] = 3.0f * t - 2.0f;
+  e[2] = 1.0f - 3.0f * t;
+  e[3] = t;
+}
+
 // Coefficient loads: FP32, or BF16 storage widened exactly to FP32 (all the
 // arithmetic stays FP32).
 __device__ __forceinline__ float load_coef(const float* p) { return __ldg(p); }
@@ -108,6 +116,48 @@ __device__ __forceinline__ float spline_sample(const C* __restrict__ c, int W, i
     *gy = ay;
   }
   return v;
+}
+
+// Value, gradient and Hessian (hxx, hxy, hyy) of the spline at
+// (bx + ox, by + oy); positions and the mirror fold as in spline_sample.
+template <class C = float>
+__device__ __forceinline__ void spline_sample_hessian(const C* __restrict__ c, int W, int H, int bx,
+                                                      int by, float ox, float oy, float& v,
+                                                      float& gx, float& gy, float& hxx,
+                                                      float& hxy, float& hyy) {
+  ox = fminf(fmaxf(ox, -1.0e7f), 1.0e7f);
+  oy = fminf(fmaxf(oy, -1.0e7f), 1.0e7f);
+  const float fx = floorf(ox), fy = floorf(oy);
+  const int ix = bx + (int)fx, iy = by + (int)fy;
+  const float tx = ox - fx, ty = oy - fy;
+  float wx[4], wy[4], dx[4], dy[4], ex[4], ey[4];
+  cubic_weights(tx, wx);
+  cubic_weights(ty, wy);
+  cubic_dweights(tx, dx);
+  cubic_dweights(ty, dy);
+  cubic_d2weights(tx, ex);
+  cubic_d2weights(ty, ey);
+  v = gx = gy = hxx = hxy = hyy = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const C* row = c + (size_t)mirror_fold(iy - 1 + m, H) * W;
+    float cc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cc[k] = load_coef(row + mirror_fold(ix - 1 + k, W));
+    float sw = 0.0f, sd = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sw += wx[k] * cc[k];
+      sd += dx[k] * cc[k];
+      se += ex[k] * cc[k];
+    }
+    v += wy[m] * sw;
+    gx += wy[m] * sd;
+    gy += dy[m] * sw;
+    hxx += wy[m] * se;
+    hxy += dy[m] * sd;
+    hyy += ey[m] * sw;
+  }
 }
 
 // Split a float coordinate into its integer cell and the exact remainder.

@@ -103,6 +103,25 @@ cudaError_t launch_count_nonfinite(const float* img, int W, int H, int64_t strid
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
                             cudaStream_t s);
 int warp_grid_blocks(int W, int H, int num_sms);
+// Adjoint of explicit iterations with the spline gradient.
+struct UnrollArgs {
+  int nV, W, H;
+  float tau, lam;
+  const float2* V;
+  const int* adj_ptr;
+  const int* adj_col;
+  const float* cTe;
+  const __nv_bfloat16* cTe16;
+  const float* ReV;
+};
+cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
+                                       float2* vout, cudaStream_t s);
+
+// Warp energy 1/2 sum (R - Re)^2 at a.u and its gradient with respect to the
+// node displacements (rg: W*H scratch, tpart: 3*nT scratch).
+cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tpart,
+                             const int* inc_ptr, const int* inc_tri, int nV, double* energy_out,
+                             float2* grad_out, cudaStream_t s);
 
 // Cluster engine (whole iteration state in the shared memory of one cluster).
 size_t cluster_smem_bytes(int form, int chunk);

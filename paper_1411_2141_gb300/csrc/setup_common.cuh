@@ -210,11 +210,32 @@ __device__ __forceinline__ void pixel_map_triangle(const float2* __restrict__ V,
         atomicMin(pix + (int64_t)y * W + x, t);
 }
 
+// Barycentric coordinates (sa, sb, sc) / (sa + sb + sc) of pixel centre
+// (x, y) in triangle (Va, Vb, Vc): corner positions are taken relative to
+// the pixel (exact differences), and each s is twice a signed sub-area.
+__device__ __forceinline__ void pixel_barycentric(float2 Va, float2 Vb, float2 Vc, int x, int y,
+                                                  float& la, float& lb, float& lc) {
+  const float fx = (float)x, fy = (float)y;
+  const float ax = Va.x - fx, ay = Va.y - fy;
+  const float bx = Vb.x - fx, by = Vb.y - fy;
+  const float cx = Vc.x - fx, cy = Vc.y - fy;
+  const float sa = bx * cy - by * cx;   // (x, b, c)
+  const float sb = cx * ay - cy * ax;   // (x, c, a)
+  const float sc = ax * by - ay * bx;   // (x, a, b)
+  const float inv = 1.0f / (sa + sb + sc);
+  la = sa * inv;
+  lb = sb * inv;
+  lc = sc * inv;
+}
+
 // Registered value R = Te(x + u(x)) at pixel p and its difference with Re
 // (step a4): P1 interpolation of the owning triangle's node displacements,
-// then the cubic B-spline of Te.  Returns false for a pixel without an owner
-// (excluded by the coverage check at set-up).
-__device__ __forceinline__ bool warp_pixel(const WarpArgs& a, int64_t p, float& R, float& d) {
+// then the cubic B-spline of Te (with GRAD also grad Te there).  Returns
+// false for a pixel without an owner (excluded by the coverage check at
+// set-up).
+template <bool GRAD = false>
+__device__ __forceinline__ bool warp_pixel(const WarpArgs& a, int64_t p, float& R, float& d,
+                                           float* gx = nullptr, float* gy = nullptr) {
   const int W = a.W, H = a.H;
   const int t = __ldg(a.pix_tri + p);
   if ((unsigned)t >= (unsigned)a.nT) return false;
@@ -222,19 +243,12 @@ __device__ __forceinline__ bool warp_pixel(const WarpArgs& a, int64_t p, float& 
   const int ia = __ldg(a.tri + 3 * t), ib = __ldg(a.tri + 3 * t + 1), ic = __ldg(a.tri + 3 * t + 2);
   const float2 Va = __ldg(a.V + ia), Vb = __ldg(a.V + ib), Vc = __ldg(a.V + ic);
   const float2 ua = __ldg(a.u + ia), ub = __ldg(a.u + ib), uc = __ldg(a.u + ic);
-  // corner positions relative to the pixel (exact differences)
-  const float fx = (float)x, fy = (float)y;
-  const float ax = Va.x - fx, ay = Va.y - fy;
-  const float bx = Vb.x - fx, by = Vb.y - fy;
-  const float cx = Vc.x - fx, cy = Vc.y - fy;
-  const float sa = bx * cy - by * cx;   // twice the area of (x, b, c)
-  const float sb = cx * ay - cy * ax;   // (x, c, a)
-  const float sc = ax * by - ay * bx;   // (x, a, b)
-  const float inv = 1.0f / (sa + sb + sc);
-  const float ux = (sa * ua.x + sb * ub.x + sc * uc.x) * inv;
-  const float uy = (sa * ua.y + sb * ub.y + sc * uc.y) * inv;
-  R = a.cTe16 ? spline_sample<false>(a.cTe16, W, H, x, y, ux, uy, nullptr, nullptr)
-              : spline_sample<false>(a.cTe, W, H, x, y, ux, uy, nullptr, nullptr);
+  float la, lb, lc;
+  pixel_barycentric(Va, Vb, Vc, x, y, la, lb, lc);
+  const float ux = la * ua.x + lb * ub.x + lc * uc.x;
+  const float uy = la * ua.y + lb * ub.y + lc * uc.y;
+  R = a.cTe16 ? spline_sample<GRAD>(a.cTe16, W, H, x, y, ux, uy, gx, gy)
+              : spline_sample<GRAD>(a.cTe, W, H, x, y, ux, uy, gx, gy);
   d = R - __ldg(a.Re + p);
   return true;
 }

@@ -70,7 +70,141 @@ __global__ void k_msd_final(const float* __restrict__ part, int nb, double inv_c
   if (lane == 0) *out = s * inv_count;
 }
 
+// ---------------------------------------------------------------- adjoint
+// Gradient of E(u) = 1/2 sum_x (Te(x + u(x)) - Re(x))^2 with respect to the
+// node displacements: dE/du_a = sum_x lambda_a(x) r(x) grad Te(x + u(x)).
+// Three passes, each with a fixed summation order (no atomics):
+//   pixels     rg(x) = r(x) grad Te(x + u(x)), and the block sums of r^2;
+//   triangles  for each corner k of triangle t, the sum of lambda_k(x) rg(x)
+//              over the pixels t owns, in row-major order of its bounding box;
+//   nodes      for each node, the sum of its corner partials over its
+//              incident triangles in ascending index order.
+
+__global__ void __launch_bounds__(kWarpBlock) k_warp_grad_pixels(const WarpArgs a,
+                                                                 float2* __restrict__ rg) {
+  __shared__ float s_red[kMaxWarps * kRec];
+  const int64_t n = (int64_t)a.W * a.H;
+  ff acc = ff_zero();
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float R, d, gx, gy;
+    if (!warp_pixel<true>(a, p, R, d, &gx, &gy)) {
+      rg[p] = make_float2(0.0f, 0.0f);
+      continue;
+    }
+    rg[p] = make_float2(d * gx, d * gy);
+    acc = ff_add(acc, ff_prod(d, d));
+  }
+  float none[1] = {0.0f};
+  block_reduce_store<1, true>(none, acc, a.part + (size_t)blockIdx.x * kRec, s_red);
+}
+
+__global__ void k_warp_grad_tris(const float2* __restrict__ V, const int* __restrict__ tri,
+                                 const int* __restrict__ pix, const float2* __restrict__ rg, int W,
+                                 int H, int nT, float2* __restrict__ tpart) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
+    const int a = __ldg(tri + 3 * t), b = __ldg(tri + 3 * t + 1), c = __ldg(tri + 3 * t + 2);
+    const float2 A = __ldg(V + a), B = __ldg(V + b), C = __ldg(V + c);
+    const int x0 = max(0, (int)ceilf(fminf(A.x, fminf(B.x, C.x))));
+    const int x1 = min(W - 1, (int)floorf(fmaxf(A.x, fmaxf(B.x, C.x))));
+    const int y0 = max(0, (int)ceilf(fminf(A.y, fminf(B.y, C.y))));
+    const int y1 = min(H - 1, (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y))));
+    float2 ga = make_float2(0.0f, 0.0f), gb = ga, gc = ga;
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const int64_t p = (int64_t)y * W + x;
+        if (__ldg(pix + p) != t) continue;
+        const float2 q = __ldg(rg + p);
+        float la, lb, lc;
+        pixel_barycentric(A, B, C, x, y, la, lb, lc);
+        ga.x += la * q.x;
+        ga.y += la * q.y;
+        gb.x += lb * q.x;
+        gb.y += lb * q.y;
+        gc.x += lc * q.x;
+        gc.y += lc * q.y;
+      }
+    tpart[3 * (size_t)t] = ga;
+    tpart[3 * (size_t)t + 1] = gb;
+    tpart[3 * (size_t)t + 2] = gc;
+  }
+}
+
+__global__ void k_warp_grad_nodes(const int* __restrict__ inc_ptr, const int* __restrict__ inc_tri,
+                                  const int* __restrict__ tri, const float2* __restrict__ tpart,
+                                  int nV, float2* __restrict__ grad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += gridDim.x * blockDim.x) {
+    float gx = 0.0f, gy = 0.0f;
+    const int e = __ldg(inc_ptr + i + 1);
+    for (int k = __ldg(inc_ptr + i); k < e; ++k) {
+      const int t = __ldg(inc_tri + k);
+      const int corner = __ldg(tri + 3 * t) == i ? 0 : (__ldg(tri + 3 * t + 1) == i ? 1 : 2);
+      const float2 q = __ldg(tpart + 3 * (size_t)t + corner);
+      gx += q.x;
+      gy += q.y;
+    }
+    grad[i] = make_float2(gx, gy);
+  }
+}
+
+// One adjoint step of an explicit (S0) iteration with the spline gradient:
+//   v_out = (I - tau D(u_k)) S^T v_in,  S = (1 - l) I + l A^Lap (Eq. 5, 14),
+//   D_j = grad Te grad Te^T + r_j Hess Te at V_j + u_k,j (the Jacobian of
+//   F_j = r_j grad Te(V_j + u_j)),
+// with (A^Lap^T v)_j = sum_{i in N1(j)} v_i / m_i (the 1-ring is symmetric).
+__global__ void k_unroll_adjoint_step(const UnrollArgs a, const float2* __restrict__ uk,
+                                      const float2* __restrict__ vin, float2* __restrict__ vout) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.nV; j += gridDim.x * blockDim.x) {
+    const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
+    float sx = 0.0f, sy = 0.0f;
+    for (int k = beg; k < end; ++k) {
+      const int i = __ldg(a.adj_col + k);
+      const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
+      const float2 vi = vin[i];
+      sx += vi.x / mi;
+      sy += vi.y / mi;
+    }
+    const float2 vj = vin[j];
+    const float wx = (1.0f - a.lam) * vj.x + a.lam * sx;
+    const float wy = (1.0f - a.lam) * vj.y + a.lam * sy;
+    const float2 V = __ldg(a.V + j), u = uk[j];
+    int bx, by;
+    float ox, oy;
+    split_coord(V.x, bx, ox);
+    split_coord(V.y, by, oy);
+    float f, gx, gy, hxx, hxy, hyy;
+    if (a.cTe16)
+      spline_sample_hessian(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
+    else
+      spline_sample_hessian(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
+    const float r = f - __ldg(a.ReV + j);
+    const float d00 = gx * gx + r * hxx, d01 = gx * gy + r * hxy, d11 = gy * gy + r * hyy;
+    vout[j] = make_float2(wx - a.tau * (d00 * wx + d01 * wy), wy - a.tau * (d01 * wx + d11 * wy));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
+                                       float2* vout, cudaStream_t s) {
+  const int g = (a.nV + 255) / 256 < 8192 ? (a.nV + 255) / 256 : 8192;
+  if (a.nV > 0) k_unroll_adjoint_step<<<g, 256, 0, s>>>(a, uk, vin, vout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tpart,
+                             const int* inc_ptr, const int* inc_tri, int nV, double* energy_out,
+                             float2* grad_out, cudaStream_t s) {
+  k_warp_grad_pixels<<<grid, kWarpBlock, 0, s>>>(a, rg);
+  if (energy_out) k_msd_final<<<1, 32, 0, s>>>(a.part, grid, 0.5, energy_out);
+  if (grad_out) {
+    const int gt = (a.nT + 127) / 128 < 8192 ? (a.nT + 127) / 128 : 8192;
+    if (a.nT > 0) k_warp_grad_tris<<<gt, 128, 0, s>>>(a.V, a.tri, a.pix_tri, rg, a.W, a.H, a.nT, tpart);
+    const int gn = (nV + 255) / 256 < 8192 ? (nV + 255) / 256 : 8192;
+    if (nV > 0) k_warp_grad_nodes<<<gn, 256, 0, s>>>(inc_ptr, inc_tri, a.tri, tpart, nV, grad_out);
+  }
+  return cudaGetLastError();
+}
 
 int warp_grid_blocks(int W, int H, int num_sms) {
   const int64_t n = (int64_t)W * H;

@@ -91,7 +91,8 @@ class mreg_stats_t(C.Structure):
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
            "mreg_msd", "mreg_energy", "mreg_get_u", "mreg_set_u", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
-           "mreg_prefilter_noalloc", "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
+           "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
+           "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
            "mreg_batch_shape", "mreg_batch_iterate_ms", "mreg_batch_msd", "mreg_batch_get_field",
            "mreg_batch_stats", "mreg_batch_destroy"]
 
@@ -134,6 +135,8 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_last_error": ([], C.c_char_p),
         "mreg_version": ([], i32),
         "mreg_prefilter_noalloc": ([vp, i64, vp, i32, i32, vp], i32),
+        "mreg_warp_energy_grad": ([vp, vp, vp, vp, vp], i32),
+        "mreg_unroll_grad": ([vp, vp, i32, vp, vp, vp], i32),
         "mreg_batch_create": ([i32, C.POINTER(mreg_mesh), C.POINTER(mreg_image),
                                C.POINTER(mreg_image), dbl, dbl, C.POINTER(mreg_options), vp,
                                C.POINTER(vp)], i32),
@@ -302,6 +305,31 @@ class Registration:
         po = out.data_ptr() if out is not None else None
         pm = msd_out.data_ptr() if msd_out is not None else None
         _check(load().mreg_warp(self._h, po, pm, _stream_ptr(stream)), "mreg_warp")
+
+    def warp_energy_grad(self, u, energy=None, grad=None, stream=None):
+        """Asynchronous E(u) into ``energy`` (1 float64 device tensor) and
+        dE/du into ``grad`` (n x 2 float32 device tensor); either may be None.
+        ``u``: n x 2 float32 contiguous device tensor."""
+        if not _is_torch_cuda(u) or str(u.dtype) != "torch.float32" or not u.is_contiguous() \
+                or tuple(u.shape) != (self.n_nodes, 2):
+            raise ValueError("u must be a contiguous (n_nodes, 2) float32 device tensor")
+        pe = energy.data_ptr() if energy is not None else None
+        pg = grad.data_ptr() if grad is not None else None
+        _check(load().mreg_warp_energy_grad(self._h, u.data_ptr(), pe, pg, _stream_ptr(stream)),
+               "mreg_warp_energy_grad")
+
+    def unroll_grad(self, u0, n_iters: int, energy=None, grad=None, stream=None):
+        """Asynchronous E(u_K) after n_iters iterations from ``u0`` into
+        ``energy`` and dE(u_K)/du0 into ``grad`` (device tensors, either may
+        be None); explicit mode with the spline gradient only.  The handle's
+        iterate is left at u_K."""
+        if not _is_torch_cuda(u0) or str(u0.dtype) != "torch.float32" or not u0.is_contiguous() \
+                or tuple(u0.shape) != (self.n_nodes, 2):
+            raise ValueError("u0 must be a contiguous (n_nodes, 2) float32 device tensor")
+        pe = energy.data_ptr() if energy is not None else None
+        pg = grad.data_ptr() if grad is not None else None
+        _check(load().mreg_unroll_grad(self._h, u0.data_ptr(), int(n_iters), pe, pg,
+                                       _stream_ptr(stream)), "mreg_unroll_grad")
 
     def msd(self, stream=None) -> float:
         v = C.c_double()
