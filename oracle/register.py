@@ -48,7 +48,7 @@ class Problem:
 
     def __init__(self, V, T, Re, Te, alpha: float, tau: float, mode: str = "S0",
                  grad: str = "G0", quad: str = "Q0", lam: float | None = None,
-                 te_sampler=None, re_sampler=None):
+                 te_sampler=None, re_sampler=None, smooth_passes: int = 1):
         if mode not in MODES:
             raise ValueError(mode)
         if quad == "Q1" and (mode != "S2" or grad != "G1"):
@@ -62,6 +62,11 @@ class Problem:
         self.alpha = float(alpha)
         self.tau = float(tau)
         self.lam = self.tau * self.alpha if lam is None else float(lam)
+        # Eq. 14 may be applied several times per iteration for a smoother
+        # field (the paper applies it once): explicit form only
+        if smooth_passes < 1 or (smooth_passes > 1 and mode != "S0"):
+            raise ValueError("smooth_passes > 1 needs the explicit form")
+        self.smooth_passes = int(smooth_passes)
         self.mode, self.grad, self.quad = mode, grad, quad
         # spline coefficients of both images (abstract: both are interpolated)
         self.cRe = bspline.prefilter_2d(self.Re)
@@ -157,7 +162,9 @@ class Problem:
     def update(self, u, F):
         if self.mode == "S0":
             u0 = u - self.tau * F
-            return (1.0 - self.lam) * u0 + self.lam * (self.Alap @ u0)
+            for _ in range(self.smooth_passes):
+                u0 = (1.0 - self.lam) * u0 + self.lam * (self.Alap @ u0)
+            return u0
         if self.mode == "S1":
             rhs = self.m[:, None] * (u - self.tau * F)
         else:

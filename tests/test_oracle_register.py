@@ -161,3 +161,55 @@ def test_generated_meshes_cover_the_image(case0):
     A = mesh.signed_area(case0.V.astype(float), case0.T)
     assert A.min() > 0
     np.testing.assert_allclose(A.sum(), 127.0 * 127.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("passes", [2, 5])
+def test_repeated_smoothing_keeps_uniform_fields_and_the_valence_weighted_sum(small, passes):
+    """Eq. 14 applied several times: A^Lap = D_m^-1 W with W symmetric, so each
+    pass keeps sum_i m_i u_i (and any uniform field); with no force the
+    update is exactly `passes` smoothing passes."""
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, "S0", "G1",
+                          lam=0.8, smooth_passes=passes)
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=(pb.n, 2))
+    out = pb.update(u, np.zeros_like(u))
+    np.testing.assert_allclose(pb.m @ out, pb.m @ u, rtol=1e-12)
+    one = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, "S0", "G1", lam=0.8)
+    ref = u
+    for _ in range(passes):
+        ref = one.update(ref, np.zeros_like(u))
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+    uniform = np.broadcast_to([0.7, -0.3], u.shape)
+    np.testing.assert_allclose(pb.update(uniform, np.zeros_like(u)), uniform, atol=1e-12)
+    # smoothing is a contraction of the non-uniform part
+    dev = lambda v: v - (pb.m @ v) / pb.m.sum()   # noqa: E731
+    assert np.linalg.norm(dev(out)) < np.linalg.norm(dev(u))
+
+
+def test_repeated_smoothing_is_explicit_only(small):
+    with pytest.raises(ValueError):
+        register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, "S1", "G0",
+                         smooth_passes=2)
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+def test_ramp_trajectory_with_repeated_smoothing(small, passes):
+    """Uniform fields are fixed by every pass, so the closed-form ramp
+    trajectory holds for any number of passes."""
+    a = np.array([0.3, -0.2])
+    b0, c, tau = 0.9, 0.4, 1.0
+
+    def te(x, y):
+        return a[0] * x + a[1] * y + b0, np.full_like(x, a[0]), np.full_like(x, a[1])
+
+    def re(x, y):
+        return a[0] * x + a[1] * y + c
+
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, tau, "S0", "G0",
+                          te_sampler=te, re_sampler=re, smooth_passes=passes)
+    n = 10
+    u, _ = pb.run(n)
+    r0 = b0 - c
+    rn = (1 - tau * a @ a) ** n * r0
+    np.testing.assert_allclose(u, np.broadcast_to(-(r0 - rn) * a / (a @ a), u.shape), rtol=1e-9,
+                               atol=1e-11)
