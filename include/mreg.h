@@ -146,6 +146,10 @@ typedef struct {
                           8; 0 = 4.  block_size is the team CTAs' size there
                           (0 = 512) and grid_blocks the number of teams (0 =
                           as many as are co-resident, at most one per pair). */
+  int32_t smooth_passes; /* explicit mode: Eq. 14 passes per iteration (the
+                          paper applies one and notes that more give a
+                          smoother field); 0 = 1, at most 64; other modes
+                          and the cluster engine accept only 1.             */
   int32_t team_blocks_per_sm; /* batched engine only: CTAs per SM that the
                           iteration kernel's register budget is sized for:
                           1 (up to 128 registers per thread) or 2 (up to 64,
@@ -248,8 +252,9 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
  * iterations of the handle's loop from u0 (explicit mode S0 with the spline
  * gradient only), evaluates E(u_K) as in mreg_warp_energy_grad, and returns
  * dE(u_K)/du0 by the adjoint recursion
- *   v_K = dE/du_K,   v_k = (I - tau D(u_k)) S^T v_{k+1},
- *   S = (1 - l) I + l A^Lap (Eq. 5, 14),  D_a = grad Te grad Te^T + r_a Hess Te
+ *   v_K = dE/du_K,   v_k = (I - tau D(u_k)) (S^T)^p v_{k+1},
+ *   S = (1 - l) I + l A^Lap (Eq. 5, 14) applied p = smooth_passes times,
+ *   D_a = grad Te grad Te^T + r_a Hess Te
  * (the Jacobian of the force of Eq. 6 with the B-spline gradient, evaluated at
  * V_a + u_k,a).  Every state u_0 .. u_{K-1} is kept on the device (8 bytes per
  * node and iteration).

@@ -20,13 +20,14 @@ the analytic derivative of the cubic B-spline.
 
 Unrolled iterations.  For the explicit form with the spline gradient (S0,
 G1: Algorithm 1 with F_a = r_a grad Te(V_a + u_a)), one iteration is
-u' = S (u - tau F(u)) with S = (1 - l) I + l A^Lap (Eq. 5, 14), so its
-Jacobian is S (I - tau D) with the 2x2 block of every node
+u' = S^p (u - tau F(u)) with S = (1 - l) I + l A^Lap (Eq. 5, 14) applied
+p = smooth_passes times (once in the paper), so its
+Jacobian is S^p (I - tau D) with the 2x2 block of every node
 
     D_a = dF_a/du_a = grad Te grad Te^T + r_a Hess Te     (at V_a + u_a),
 
 and the gradient of E(u_K) with respect to the starting u_0 is the adjoint
-recursion v_K = dE/du_K, v_k = (I - tau D(u_k)) S^T v_{k+1}, returned as v_0.
+recursion v_K = dE/du_K, v_k = (I - tau D(u_k)) (S^T)^p v_{k+1}, returned as v_0.
 
 Pinned by ``tests/test_oracle_adjoint.py``: FP64 central differences of E
 and of E(u_K(u_0)), zero gradient on identical images, the sum over nodes
@@ -99,7 +100,9 @@ def unrolled_grad(pb, u0, n_iter: int):
     E, v = warp_energy_grad(pb, u)
     AlapT = pb.Alap.T.tocsr()
     for uk in reversed(states):
-        w = (1.0 - pb.lam) * v + pb.lam * (AlapT @ v)        # S^T v
+        w = v
+        for _ in range(pb.smooth_passes):                     # (S^T)^passes v
+            w = (1.0 - pb.lam) * w + pb.lam * (AlapT @ w)
         P = pb.V + uk
         f, gx, gy = bspline.evaluate(pb.cTe, P[:, 0], P[:, 1], grad=True)
         hxx, hxy, hyy = bspline.hessian(pb.cTe, P[:, 0], P[:, 1])

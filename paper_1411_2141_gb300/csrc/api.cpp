@@ -116,24 +116,22 @@ mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam
       }
   }
 
-  // node graph: the 1-ring N1(i) of Eq. 11, ascending
+  // node graph: the 1-ring N1(i) of Eq. 11, ascending, from the other two
+  // corners of every incident triangle (sorted, duplicates removed in place)
   {
-    std::vector<std::vector<int>> nb(nV);
-    for (int t = 0; t < nT; ++t) {
-      const int a = m.tri[3 * (size_t)t], b = m.tri[3 * (size_t)t + 1], c = m.tri[3 * (size_t)t + 2];
-      nb[a].push_back(b), nb[a].push_back(c);
-      nb[b].push_back(a), nb[b].push_back(c);
-      nb[c].push_back(a), nb[c].push_back(b);
-    }
+    m.adj_col.assign(m.inc_opp.begin(), m.inc_opp.end());   // 2 candidates per incidence
     m.adj_ptr.assign(nV + 1, 0);
+    int out = 0;
     for (int i = 0; i < nV; ++i) {
-      std::sort(nb[i].begin(), nb[i].end());
-      nb[i].erase(std::unique(nb[i].begin(), nb[i].end()), nb[i].end());
-      m.adj_ptr[i + 1] = m.adj_ptr[i] + (int)nb[i].size();
+      int* b = m.adj_col.data() + 2 * (size_t)m.inc_ptr[i];
+      int* e = m.adj_col.data() + 2 * (size_t)m.inc_ptr[i + 1];
+      std::sort(b, e);
+      e = std::unique(b, e);
+      for (int* q = b; q != e; ++q) m.adj_col[out++] = *q;   // out <= 2 inc_ptr[i] <= q
+      m.adj_ptr[i + 1] = out;
     }
-    m.nnz = m.adj_ptr[nV];
+    m.nnz = out;
     m.adj_col.resize(m.nnz);
-    for (int i = 0; i < nV; ++i) std::copy(nb[i].begin(), nb[i].end(), m.adj_col.begin() + m.adj_ptr[i]);
   }
   // unique edges (a < b) and the edge id of every adjacency entry
   m.adj_edge.assign(m.nnz, -1);
@@ -268,6 +266,7 @@ struct mreg_handle {
   double* last = nullptr;
   double* energy_hist = nullptr;
   float2* epart = nullptr;   // grid engine: per-warp energy partials of one launch
+  float2* us = nullptr;      // scratch of repeated smoothing passes
   int* pcg_it_hist = nullptr;
   double* pcg_res_hist = nullptr;
   float* warp_part = nullptr;
@@ -286,6 +285,7 @@ struct mreg_handle {
     a.n_iters = n_iters;
     a.maxit = opts.pcg_maxit;
     a.hist_cap = kHistCap;
+    a.smooth_passes = opts.smooth_passes > 0 ? opts.smooth_passes : 1;
     a.tau = (float)tau;
     a.lam = (float)lam;
     a.area_floor = area_floor;
@@ -314,6 +314,7 @@ struct mreg_handle {
     a.f = f;
     a.F = F;
     a.u0 = u0;
+    a.us = us;
     a.hq = hq;
     a.cg = cg;
     a.rt = rt;
@@ -373,6 +374,10 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
     return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
+  if (o.smooth_passes < 0 || o.smooth_passes > 64)
+    return fail(MREG_ERR_INVALID_ARG, "smooth_passes must be in [0, 64]");
+  if (o.smooth_passes > 1 && o.mode != MREG_MODE_EXPLICIT)
+    return fail(MREG_ERR_INVALID_ARG, "smooth_passes > 1 needs the explicit mode");
   const double l = o.lambda < 0.0 ? tau * alpha : o.lambda;
   if (!std::isfinite(l)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
   *lam = l;
@@ -535,6 +540,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   // cluster engine: the whole iteration state in one cluster's shared memory
   // AUTO runs the grid engine: on the 512^2 / 20k-node pair it measured 41 us per
   // iteration against 74 us for the cluster engine (16 SMs are ALU-bound there).
+  if (o.engine == MREG_ENGINE_CLUSTER && o.smooth_passes > 1)
+    return fail(MREG_ERR_INVALID_ARG, "the cluster engine runs one smoothing pass per iteration");
   if (o.engine == MREG_ENGINE_CLUSTER && h->form != mreg::kFormFemEdges) {
     int smem_optin = 0;
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev),
@@ -580,7 +587,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_lump = take(nV * 4), o_Md = take(nV * 4), o_Mo = take(nnz * 4),
                o_Ad = take(nV * 4), o_Ao = take(nnz * 4), o_dinv = take(nV * 4),
                o_ReV = take(nV * 4), o_ReQ = take(nE * 4), o_f = take(nV * 4), o_u = take(nV * 8),
-               o_F = take(2 * nV * 8), o_u0 = take(2 * nV * 8), o_hq = take(nE * 8),
+               o_F = take(2 * nV * 8), o_u0 = take(2 * nV * 8), o_us = take(nV * 8), o_hq = take(nE * 8),
                o_cg = take(2 * 3 * nV * 16), o_rt = take(nV * 8), o_b = take(nV * 16),
                o_part = take((size_t)2 * h->grid * mreg::kRec * 4), o_bar = take(8),
                o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
@@ -618,6 +625,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->u = (float2*)(base + o_u);
   h->F = (float2*)(base + o_F);
   h->u0 = (float2*)(base + o_u0);
+  h->us = (float2*)(base + o_us);
   h->hq = (float2*)(base + o_hq);
   h->cg = (float4*)(base + o_cg);
   h->rt = (float2*)(base + o_rt);
@@ -733,7 +741,7 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t vec = align_up(sizeof(float2) * h->nV);
-  const size_t need = vec * ((size_t)n_iters + 2);
+  const size_t need = vec * ((size_t)n_iters + 3);
   if (need > h->unroll_bytes) {
     CK(cudaStreamSynchronize(s), "synchronize");
     if (h->unroll_buf) cudaFree(h->unroll_buf);
@@ -745,6 +753,7 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   char* base = (char*)h->unroll_buf;
   float2* va = (float2*)(base + vec * n_iters);
   float2* vb = (float2*)(base + vec * (n_iters + 1));
+  float2* vc = (float2*)(base + vec * (n_iters + 2));
   // forward: u_0 .. u_{K-1} kept, the handle's iteration runs one step at a time
   CK(cudaMemcpyAsync(h->u, u0_dev, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s), "copy u0");
   for (int k = 0; k < n_iters; ++k) {
@@ -768,7 +777,12 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   a.cTe = h->cTe;
   a.cTe16 = h->cTe16;
   a.ReV = h->ReV;
+  const int passes = h->opts.smooth_passes > 0 ? h->opts.smooth_passes : 1;
   for (int k = n_iters - 1; k >= 0; --k) {
+    for (int p = 1; p < passes; ++p) {   // the repeated passes' S^T, then the fused step
+      CK(mreg::launch_unroll_smooth_t(a, va, vc, s), "adjoint smoothing launch");
+      std::swap(va, vc);
+    }
     CK(mreg::launch_unroll_adjoint_step(a, (const float2*)(base + vec * k), va, vb, s),
        "adjoint step launch");
     std::swap(va, vb);

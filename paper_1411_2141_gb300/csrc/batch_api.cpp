@@ -4,11 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "host_common.h"
@@ -247,27 +250,56 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
     return fail(MREG_ERR_INVALID_ARG, "team_blocks_per_sm must be 0, 1 or 2");
 
-  // host topology of every pair
+  // host topology of every pair, built on worker threads (pairs are
+  // independent); the first failing pair (lowest index) is reported
   std::vector<HostMesh> hm(n_pairs);
-  for (int p = 0; p < n_pairs; ++p) {
-    const mreg_mesh* m = meshes + p;
-    if (!m->xy || !m->tri)
-      return fail(MREG_ERR_INVALID_ARG, "pair %d: mesh arrays are NULL", p);
-    if (m->n_nodes < 3 || m->n_tris < 1)
-      return fail(MREG_ERR_INVALID_ARG, "pair %d: mesh needs >= 3 nodes and >= 1 triangle", p);
-    st = validate_image(Re + p, "Re");
-    if (!st) st = validate_image(Te + p, "Te");
-    if (st) return fail(st, "pair %d: %s", p, mreg_last_error());
-    if (Re[p].width != Te[p].width || Re[p].height != Te[p].height)
-      return fail(MREG_ERR_SIZE_MISMATCH, "pair %d: Re is %dx%d but Te is %dx%d", p, Re[p].width,
-                  Re[p].height, Te[p].width, Te[p].height);
+  std::vector<mreg_status> pst(n_pairs, MREG_OK);
+  std::vector<std::string> pmsg(n_pairs);
+  {
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      for (;;) {
+        const int p = next.fetch_add(1);
+        if (p >= n_pairs) return;
+        const mreg_mesh* m = meshes + p;
+        mreg_status s2 = MREG_OK;
+        if (!m->xy || !m->tri) {
+          s2 = fail(MREG_ERR_INVALID_ARG, "mesh arrays are NULL");
+        } else if (m->n_nodes < 3 || m->n_tris < 1) {
+          s2 = fail(MREG_ERR_INVALID_ARG, "mesh needs >= 3 nodes and >= 1 triangle");
+        } else {
+          s2 = validate_image(Re + p, "Re");
+          if (!s2) s2 = validate_image(Te + p, "Te");
+          if (!s2 && (Re[p].width != Te[p].width || Re[p].height != Te[p].height))
+            s2 = fail(MREG_ERR_SIZE_MISMATCH, "Re is %dx%d but Te is %dx%d", Re[p].width,
+                      Re[p].height, Te[p].width, Te[p].height);
+          if (!s2) {
+            try {
+              s2 = build_mesh(m, Re[p].width, Re[p].height, o.mode, lam, hm[p]);
+            } catch (const std::bad_alloc&) {
+              s2 = fail(MREG_ERR_OOM, "host allocation failed while building the mesh topology");
+            }
+          }
+        }
+        if (s2) {
+          pst[p] = s2;
+          pmsg[p] = mreg_last_error();   // this worker's thread-local message
+        }
+      }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nthreads = (int)std::min<unsigned>(std::min<unsigned>(hw, 32u), (unsigned)n_pairs);
+    std::vector<std::thread> pool;
     try {
-      st = build_mesh(m, Re[p].width, Re[p].height, o.mode, lam, hm[p]);
-    } catch (const std::bad_alloc&) {
-      return fail(MREG_ERR_OOM, "host allocation failed while building the mesh topology");
+      for (int k = 1; k < nthreads; ++k) pool.emplace_back(work);
+    } catch (const std::system_error&) {
+      // fewer threads than asked for: the calling thread does the rest
     }
-    if (st) return fail(st, "pair %d: %s", p, mreg_last_error());
+    work();
+    for (auto& t : pool) t.join();
   }
+  for (int p = 0; p < n_pairs; ++p)
+    if (pst[p]) return fail(pst[p], "pair %d: %s", p, pmsg[p].c_str());
 
   mreg_batch* b = new (std::nothrow) mreg_batch();
   if (!b) return fail(MREG_ERR_OOM, "host allocation failed");
@@ -352,7 +384,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   const size_t o_V = take(NN * 8), o_ReV = take(NN * 4), o_f = take(NN * 4), o_u = take(NN * 8),
                o_rt = take(NN * 8), o_dinv = take(NN * 4), o_lump = take(NN * 4),
                o_Md = take(NN * 4), o_Ad = take(NN * 4), o_F = take(2 * NN * 8),
-               o_u0 = take(2 * NN * 8), o_cg = take(6 * NN * 16), o_b = take(NN * 16),
+               o_u0 = take(2 * NN * 8), o_us = take(NN * 8), o_cg = take(6 * NN * 16), o_b = take(NN * 16),
                o_incp = take((NN + P) * 4), o_adjp = take((NN + P) * 4);
   const size_t o_adjc = take(NZ * 4), o_adje = take(NZ * 4), o_Mo = take(NZ * 4),
                o_Ao = take(NZ * 4);
@@ -404,6 +436,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
     a.H = I.H;
     a.maxit = o.pcg_maxit;
     a.hist_cap = kBatchHist;
+    a.smooth_passes = o.smooth_passes > 0 ? o.smooth_passes : 1;
     a.tau = (float)tau;
     a.lam = (float)lam;
     a.area_floor = I.area_floor;
@@ -432,6 +465,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
     a.f = F32(o_f) + I.node;
     a.F = (float2*)(base + o_F) + 2 * I.node;
     a.u0 = (float2*)(base + o_u0) + 2 * I.node;
+    a.us = (float2*)(base + o_us) + I.node;
     a.hq = (float2*)(base + o_hq) + I.edge;
     a.cg = (float4*)(base + o_cg) + 6 * I.node;
     a.rt = (float2*)(base + o_rt) + I.node;

@@ -194,8 +194,32 @@ __device__ __forceinline__ float2 neighbour_force_c(const IterArgs& a, const Top
 #define FOR_NODES(i, cached) \
   for (int i = tid, slot_ = 0; i < nV; i += nth, ++slot_) if (const bool cached = slot_ == 0; true)
 
+// One Eq. 14 pass at node i: (1 - l) v_i + l mean_{j in N1(i)} v_j.
+__device__ __forceinline__ float2 smooth_node(const IterArgs& a, const Topo& T, bool cached,
+                                              const float2* v, int i, float lam) {
+  int beg, deg;
+  T.arow(a, cached, i, beg, deg);
+  float sx = 0.0f, sy = 0.0f;
+  for (int k0 = 0; k0 < deg; k0 += 4) {
+    float2 w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = (k0 + u < deg) ? v[T.adj(a, cached, beg, k0 + u)] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u < deg) {
+        sx += w[u].x;
+        sy += w[u].y;
+      }
+    }
+  }
+  const float inv_m = 1.0f / (float)deg;
+  const float2 c = v[i];
+  return make_float2((1.0f - lam) * c.x + lam * (sx * inv_m), (1.0f - lam) * c.y + lam * (sy * inv_m));
+}
+
 // ======================================================================
-// S0: explicit step and one umbrella smoothing pass (Algorithm 1 exactly)
+// S0: explicit step and umbrella smoothing passes (Algorithm 1; one pass by
+// default, as in the paper)
 // ======================================================================
 template <int GRAD, class TEAM>
 __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsigned char* dsm) {
@@ -238,29 +262,19 @@ __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsi
       }
       SYNC_OR_LEAVE();   // u0 of every node is needed below
     }
-    // one umbrella smoothing pass (Eq. 14), then the next sample
-    ff e = ff_zero();
+    // umbrella smoothing (Eq. 14): smooth_passes - 1 passes between scratch
+    // buffers, then the last pass into u with the next sample
     const float lam = a.lam;
+    const float2* src = u0;
+    for (int pass = 1; pass < a.smooth_passes; ++pass) {
+      float2* dst = (pass & 1) ? a.us : u0;   // u0 is free once pass 1 has read it
+      FOR_NODES(i, cached) dst[i] = smooth_node(a, T, cached, src, i, lam);
+      SYNC_OR_LEAVE();
+      src = dst;
+    }
+    ff e = ff_zero();
     FOR_NODES(i, cached) {
-      int beg, deg;
-      T.arow(a, cached, i, beg, deg);
-      float sx = 0.0f, sy = 0.0f;
-      for (int k0 = 0; k0 < deg; k0 += 4) {
-        float2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (k0 + u < deg) ? u0[T.adj(a, cached, beg, k0 + u)] : make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (k0 + u < deg) {
-            sx += v[u].x;
-            sy += v[u].y;
-          }
-        }
-      }
-      const float inv_m = 1.0f / (float)deg;
-      const float2 c = u0[i];
-      const float2 un = make_float2((1.0f - lam) * c.x + lam * (sx * inv_m),
-                                    (1.0f - lam) * c.y + lam * (sy * inv_m));
+      const float2 un = smooth_node(a, T, cached, src, i, lam);
       a.u[i] = un;
       float2 Fv;
       e = ff_add_f(e, sample_node<kFormExplicit, GRAD>(a, i, un, a.f + i, Fn + i, &Fv));

@@ -29,6 +29,7 @@ enum Form : int {
 // Everything the persistent iteration kernel reads or writes.
 struct IterArgs {
   int nV, nE, W, H, n_iters, it0, maxit, hist_cap;   // it0: history index of iteration 0
+  int smooth_passes;     // S0: Eq. 14 passes per iteration (>= 1)
   int chunk;             // cluster engine: nodes per CTA
   float inv_chunk;       // 1 / chunk
   float tau, lam, area_floor, rtol2;
@@ -58,6 +59,7 @@ struct IterArgs {
   float* f;              // Te(V+u)
   float2* F;             // force, two buffers of nV (iteration parity)
   float2* u0;            // S0: u - tau F, two buffers of nV (iteration parity)
+  float2* us;            // S0: scratch of the repeated smoothing passes (nV)
   float2* hq;            // edge form: per-edge force contribution
   float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s}
   float2* rt;            // true residual (FP32 copy) for restarts
@@ -116,6 +118,8 @@ struct UnrollArgs {
 };
 cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
                                        float2* vout, cudaStream_t s);
+cudaError_t launch_unroll_smooth_t(const UnrollArgs& a, const float2* vin, float2* vout,
+                                   cudaStream_t s);
 
 // Warp energy 1/2 sum (R - Re)^2 at a.u and its gradient with respect to the
 // node displacements (rg: W*H scratch, tpart: 3*nT scratch).

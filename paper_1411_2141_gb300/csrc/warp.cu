@@ -183,7 +183,33 @@ __global__ void k_unroll_adjoint_step(const UnrollArgs a, const float2* __restri
   }
 }
 
+// One transposed Eq. 14 pass: v_out = S^T v_in (the repeated passes of an
+// iteration with smooth_passes > 1 apply it before the fused step above).
+__global__ void k_unroll_smooth_t(const UnrollArgs a, const float2* __restrict__ vin,
+                                  float2* __restrict__ vout) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.nV; j += gridDim.x * blockDim.x) {
+    const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
+    float sx = 0.0f, sy = 0.0f;
+    for (int k = beg; k < end; ++k) {
+      const int i = __ldg(a.adj_col + k);
+      const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
+      const float2 vi = vin[i];
+      sx += vi.x / mi;
+      sy += vi.y / mi;
+    }
+    const float2 vj = vin[j];
+    vout[j] = make_float2((1.0f - a.lam) * vj.x + a.lam * sx, (1.0f - a.lam) * vj.y + a.lam * sy);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_unroll_smooth_t(const UnrollArgs& a, const float2* vin, float2* vout,
+                                   cudaStream_t s) {
+  const int g = (a.nV + 255) / 256 < 8192 ? (a.nV + 255) / 256 : 8192;
+  if (a.nV > 0) k_unroll_smooth_t<<<g, 256, 0, s>>>(a, vin, vout);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
                                        float2* vout, cudaStream_t s) {

@@ -77,7 +77,7 @@ class mreg_options(C.Structure):
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
                 ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
-                ("team_blocks_per_sm", C.c_int32)]
+                ("smooth_passes", C.c_int32), ("team_blocks_per_sm", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -204,7 +204,8 @@ def default_options() -> mreg_options:
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
-                 coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0) -> mreg_options:
+                 coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0,
+                 smooth_passes=0) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -221,6 +222,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.coeff_bf16 = int(bool(coeff_bf16))
     o.team_ctas = int(team_ctas)
     o.team_blocks_per_sm = int(team_blocks_per_sm)
+    o.smooth_passes = int(smooth_passes)
     return o
 
 

@@ -175,3 +175,16 @@ def test_unrolled_autograd_and_mode_check(mreg, case0):
     with mreg.Registration(case0.V, case0.T, case0.Re, case0.Te, 0.1, 1.0, mode="S1") as r:
         with pytest.raises(mreg.MregError):
             r.unroll_grad(torch.zeros(case0.n_nodes, 2, device="cuda"), 3)
+
+
+def test_unrolled_gradient_with_repeated_smoothing(mreg, case0):
+    pb = register.Problem(case0.V, case0.T, case0.Re, case0.Te, case0.spec.alpha,
+                          case0.spec.tau, "S0", "G1", smooth_passes=3)
+    u0 = _smooth_u(case0, 0.5, 13)
+    _, g_ref = adjoint.unrolled_grad(pb, u0.astype(np.float64), 10)
+    with mreg.Registration(case0.V, case0.T, case0.Re, case0.Te, case0.spec.alpha,
+                           case0.spec.tau, mode="S0", grad="G1", smooth_passes=3) as r:
+        g = torch.empty(case0.n_nodes, 2, device="cuda")
+        r.unroll_grad(torch.from_numpy(u0).cuda(), 10, None, g)
+        g = g.cpu().numpy()
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()

@@ -102,8 +102,10 @@ def test_spline_hessian_matches_differences_of_the_gradient(small_case):
     np.testing.assert_allclose(hyy[ok], ((gyq - gyr) / (2 * h))[ok], atol=1e-6 * sc)
 
 
-def test_unrolled_gradient_matches_central_differences(small_case):
-    pb = _problem(small_case)
+@pytest.mark.parametrize("passes", [1, 3])
+def test_unrolled_gradient_matches_central_differences(small_case, passes):
+    c = small_case
+    pb = register.Problem(c.V, c.T, c.Re, c.Te, 0.1, 1.0, "S0", "G1", smooth_passes=passes)
     u0 = _smooth_u(small_case, amp=0.5, seed=9)
     K = 5
     _, g = adjoint.unrolled_grad(pb, u0, K)
