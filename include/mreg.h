@@ -150,6 +150,11 @@ typedef struct {
                           paper applies one and notes that more give a
                           smoother field); 0 = 1, at most 64; other modes
                           and the cluster engine accept only 1.             */
+  int32_t host_topology; /* 0: the mesh pre-computation of Algorithm 1
+                          (incidence and 1-ring CSRs, edges, quadrature
+                          weights, operators) runs on the device; 1: on the
+                          host.  Both give the same arrays bit for bit.  The
+                          batched engine always builds on the host.  (default 0) */
   int32_t team_blocks_per_sm; /* batched engine only: CTAs per SM that the
                           iteration kernel's register budget is sized for:
                           1 (up to 128 registers per thread) or 2 (up to 64,

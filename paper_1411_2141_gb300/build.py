@@ -20,7 +20,7 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libmreg.so")
 
 SOURCES = ["api.cpp", "batch_api.cpp", "prefilter.cu", "iterate.cu", "iterate_cluster.cu",
-           "batch.cu", "warp.cu", "prefilter_noalloc.cu"]
+           "batch.cu", "warp.cu", "topology.cu", "prefilter_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -45,6 +45,8 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
         obj = os.path.join(OBJDIR, src.rsplit(".", 1)[0] + ".o")
         objs.append(obj)
         cmd = [nvcc(), *ARCH, *COMMON, "-lineinfo", "-c", os.path.join(CSRC, src), "-o", obj]
+        if src.endswith(".cpp"):   # host FP64 sums without contraction, as on the device
+            cmd[1:1] = ["-Xcompiler", "-ffp-contract=off"]
         if ptxas_info and src.endswith(".cu"):
             cmd[1:1] = ["-Xptxas", "-v"]
         if verbose:

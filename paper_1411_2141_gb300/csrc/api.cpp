@@ -49,7 +49,8 @@ static int find_in_row(const HostMesh& m, int i, int j) {
   return (p != e && *p == j) ? (int)(p - m.adj_col.data()) : -1;
 }
 
-mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m) {
+mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m,
+                       bool topology) {
   m.nV = mesh->n_nodes;
   m.nT = mesh->n_tris;
   const int nV = m.nV, nT = m.nT;
@@ -94,6 +95,7 @@ mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam
                 "triangle areas sum to %.9g but the image domain has area %.9g: the mesh does "
                 "not tile the image",
                 total, domain);
+  if (!topology) return MREG_OK;   // built on the device
 
   // incident triangles of every node, ascending triangle index (Eq. 10)
   m.inc_ptr.assign(nV + 1, 0);
@@ -374,6 +376,8 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
     return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
+  if (o.host_topology != 0 && o.host_topology != 1)
+    return fail(MREG_ERR_INVALID_ARG, "host_topology must be 0 or 1");
   if (o.smooth_passes < 0 || o.smooth_passes > 64)
     return fail(MREG_ERR_INVALID_ARG, "smooth_passes must be in [0, 64]");
   if (o.smooth_passes > 1 && o.mode != MREG_MODE_EXPLICIT)
@@ -486,9 +490,10 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   st = validate_options(o, alpha, tau, &lam);
   if (st) return st;
   const int W = Re->width, H = Re->height;
+  const bool dev_topo = o.host_topology == 0;
   HostMesh hm;
   try {
-    st = build_mesh(mesh, W, H, o.mode, lam, hm);
+    st = build_mesh(mesh, W, H, o.mode, lam, hm, !dev_topo);
   } catch (const std::bad_alloc&) {
     return fail(MREG_ERR_OOM, "host allocation failed while building the mesh topology");
   }
@@ -571,8 +576,10 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   }
 
   // one arena for every device array
-  const size_t npx = (size_t)W * H, nV = hm.nV, nT = hm.nT, nE = std::max(hm.nE, 1),
-               nnz = std::max(hm.nnz, 1);
+  // the device build writes into arrays sized for its capacities
+  const size_t npx = (size_t)W * H, nV = hm.nV, nT = hm.nT,
+               nE = dev_topo ? 3 * nT : (size_t)std::max(hm.nE, 1),
+               nnz = dev_topo ? 6 * nT : (size_t)std::max(hm.nnz, 1);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o2 = off;
@@ -652,6 +659,41 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   };
   CK(up(h->V, hm.xy.data(), nV * 8), "upload");
   CK(up(h->tri, hm.tri.data(), nT * 12), "upload");
+  if (dev_topo) {
+    void* scratch = nullptr;
+    CK(cudaMalloc(&scratch, mreg::topology_scratch_bytes(h->nV, h->nT)), "device allocation");
+    mreg::TopoArgs ta{};
+    ta.nV = h->nV;
+    ta.nT = h->nT;
+    ta.form = h->form;
+    ta.lam = lam;
+    ta.V = h->V;
+    ta.tri = h->tri;
+    ta.inc_ptr = h->inc_ptr;
+    ta.inc_tri = h->inc_tri;
+    ta.inc_opp = h->inc_opp;
+    ta.adj_ptr = h->adj_ptr;
+    ta.adj_col = h->adj_col;
+    ta.adj_edge = h->adj_edge;
+    ta.edges = h->edges;
+    ta.edge_w = h->edge_w;
+    ta.lumped = h->lumped;
+    ta.Mdiag = h->Mdiag;
+    ta.Moff = h->Moff;
+    ta.Adiag = h->Adiag;
+    ta.Aoff = h->Aoff;
+    ta.dinv = h->dinv;
+    ta.flags = h->counters;
+    int flags[4] = {0, 0, 0, 0};
+    cudaError_t e = mreg::build_topology(ta, scratch, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags, h->counters, sizeof flags, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    CK(e, "device mesh pre-computation");
+    if (flags[0]) return fail(MREG_ERR_BAD_MESH, "%d nodes belong to no triangle", flags[0]);
+    h->nnz = flags[1];
+    h->nE = flags[2];
+  } else {
   CK(up(h->inc_ptr, hm.inc_ptr.data(), (nV + 1) * 4), "upload");
   CK(up(h->inc_opp, hm.inc_opp.data(), nT * 24), "upload");
   CK(up(h->inc_tri, hm.inc_tri.data(), nT * 12), "upload");
@@ -666,6 +708,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   CK(up(h->Adiag, hm.Adiag.data(), nV * 4), "upload");
   CK(up(h->Aoff, hm.Aoff.data(), (size_t)hm.nnz * 4), "upload");
   CK(up(h->dinv, hm.dinv.data(), nV * 4), "upload");
+  }
   st = device_setup(h, s, true);
   if (st) return st;
   guard.keep = true;

@@ -35,9 +35,12 @@ struct HostMesh {
 // Record the message returned by mreg_last_error(); returns st.
 mreg_status fail(mreg_status st, const char* fmt, ...);
 mreg_status cuda_fail(cudaError_t e, const char* what);
-// Validates and copies the mesh and builds its topology and operators for
-// the given mode and smoothing weight.
-mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m);
+// Validates and copies the mesh (nodes in the image, indices, orientation,
+// areas, coverage of the image) and, with topology, builds its incidence and
+// 1-ring CSRs, edges, quadrature weights and operators for the given mode and
+// smoothing weight.
+mreg_status build_mesh(const mreg_mesh* mesh, int W, int H, int mode, double lam, HostMesh& m,
+                       bool topology = true);
 // Size, stride and (host images) finiteness checks.
 mreg_status validate_image(const mreg_image* im, const char* name);
 // Option checks shared by every entry point that takes mreg_options;

@@ -90,6 +90,27 @@ struct WarpArgs {
   float* part;           // one reduction record (kRec floats) per block
 };
 
+// Device build of the mesh pre-computation (Algorithm 1): incidence and
+// 1-ring CSRs, edges, quadrature weights, operators.  Arrays sized for the
+// capacities 3 nT incidences, 6 nT 1-ring entries, 3 nT edges.
+struct TopoArgs {
+  int nV, nT, form;      // form: kForm*
+  double lam;
+  const float2* V;
+  const int* tri;        // counter-clockwise
+  int* inc_ptr;          // nV + 1
+  int* inc_tri;          // incident triangle ids, ascending per node
+  int2* inc_opp;         // the other two corners of each incidence
+  int* adj_ptr;          // nV + 1
+  int* adj_col;
+  int* adj_edge;
+  int2* edges;
+  float *edge_w, *lumped, *Mdiag, *Moff, *Adiag, *Aoff, *dinv;
+  int* flags;            // device, 4 ints: [0] nodes in no triangle, [1] 1-ring entries, [2] edges
+};
+size_t topology_scratch_bytes(int nV, int nT);
+cudaError_t build_topology(const TopoArgs& a, void* scratch, cudaStream_t s);
+
 // Launchers (return the first CUDA error, cudaSuccess otherwise).
 cudaError_t launch_prefilter(const float* img, int64_t stride, float* tmp, float* coef, int W,
                              int H, cudaStream_t s);

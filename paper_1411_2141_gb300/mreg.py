@@ -77,7 +77,8 @@ class mreg_options(C.Structure):
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
                 ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
-                ("smooth_passes", C.c_int32), ("team_blocks_per_sm", C.c_int32)]
+                ("smooth_passes", C.c_int32), ("host_topology", C.c_int32),
+                ("team_blocks_per_sm", C.c_int32)]
 
 
 class mreg_stats_t(C.Structure):
@@ -205,7 +206,7 @@ def default_options() -> mreg_options:
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
                  coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0,
-                 smooth_passes=0) -> mreg_options:
+                 smooth_passes=0, host_topology=False) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -223,6 +224,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.team_ctas = int(team_ctas)
     o.team_blocks_per_sm = int(team_blocks_per_sm)
     o.smooth_passes = int(smooth_passes)
+    o.host_topology = int(bool(host_topology))
     return o
 
 

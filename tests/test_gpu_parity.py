@@ -369,3 +369,25 @@ def test_paper_parameters_on_8bit_intensities(mreg, c0, grad, n):
     assert abs(msd - msd_ref) / msd_ref <= MSD_RTOL
     if grad == "G0":
         assert msd < pb.msd(np.zeros_like(u_ref))
+
+
+@pytest.mark.parametrize("mode,grad,quad", [("S0", "G0", "Q0"), ("S1", "G0", "Q0"),
+                                            ("S2", "G0", "Q0"), ("S2", "G1", "Q1")])
+def test_device_and_host_mesh_precomputation_agree_bitwise(mreg, c0, mode, grad, quad):
+    """Algorithm 1's pre-computation built on the device and on the host give
+    the same arrays (incidence order, 1-rings, edge ids, FP64-summed weights
+    and operators), hence bitwise the same registration."""
+    out = []
+    for host in (False, True):
+        with _reg(mreg, c0, mode, grad, quad, host_topology=host) as r:
+            r.step(20)
+            out.append((r.get_u(), r.msd(), r.get_field(mreg.MREG_FIELD_ENERGY),
+                        r.get_field(mreg.MREG_FIELD_FORCE)))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_device_precomputation_rejects_a_node_outside_every_triangle(mreg, c0):
+    V = np.concatenate([c0.V, [[5.5, 7.25]]]).astype(np.float32)   # unused extra node
+    with pytest.raises(mreg.MregError, match="no triangle"):
+        mreg.Registration(V, c0.T, c0.Re, c0.Te, 0.1, 1.0)
