@@ -131,7 +131,8 @@ typedef struct {
   double pcg_rtol;     /* stop when ||b - A u'||_2 <= rtol ||b||_2, residual
                           formed in FP64, per component     (default 1e-7)  */
   int32_t block_size;  /* threads per block of the iteration kernel (multiple of
-                          32, <= 512); 0 = 256                              */
+                          32, <= 512); 0 = 256, or 512 when the mesh has more
+                          nodes than 256 per SM                             */
   int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
   int32_t engine;      /* MREG_ENGINE_*                     (default AUTO)  */
   int32_t coeff_bf16;  /* 1: the iteration and the warp read Te's B-spline
@@ -155,10 +156,11 @@ typedef struct {
                           weights, operators) runs on the device; 1: on the
                           host.  Both give the same arrays bit for bit.  The
                           batched engine always builds on the host.  (default 0) */
-  int32_t team_blocks_per_sm; /* batched engine only: CTAs per SM that the
-                          iteration kernel's register budget is sized for:
-                          1 (up to 128 registers per thread) or 2 (up to 64,
-                          the rest in local memory); 0 = 1.                 */
+  int32_t team_blocks_per_sm; /* grid and batched engines: blocks per SM
+                          that the iteration kernel's register budget is
+                          sized for: 1 (up to 128 registers per thread) or 2
+                          (up to 64, the rest in local memory); 0 = 1 (the
+                          batched engine's autotuner tries both).           */
 } mreg_options;
 
 typedef struct {

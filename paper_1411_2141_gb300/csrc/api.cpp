@@ -238,6 +238,7 @@ struct mreg_handle {
   double alpha = 0.0, tau = 0.0, lam = 0.0;
   int form = 0, grad = 0;
   int grid = 0, block = 0, warp_grid = 0;
+  int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
   int engine = MREG_ENGINE_GRID, cl_size = 0, cl_chunk = 0;
   float area_floor = 0.0f;
   int iterations_done = 0, last_n_iters = 0, last_force_buf = 0;
@@ -376,6 +377,8 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
     return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
+  if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
+    return fail(MREG_ERR_INVALID_ARG, "team_blocks_per_sm must be 0, 1 or 2");
   if (o.host_topology != 0 && o.host_topology != 1)
     return fail(MREG_ERR_INVALID_ARG, "host_topology must be 0 or 1");
   if (o.smooth_passes < 0 || o.smooth_passes > 64)
@@ -529,10 +532,17 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                 : (o.quad == MREG_QUAD_EDGE_MIDPOINTS ? mreg::kFormFemEdges : mreg::kFormFemNodes);
   h->area_floor = (float)hm.area_floor;
 
-  // launch shape of the iteration kernel
-  h->block = o.block_size ? o.block_size : 256;
+  // launch shape of the iteration kernel.  Measured on GB300 (S1, grid
+  // engine): blocks of 256 on the 512^2 / 20k-node pair (35.5 us/iteration
+  // against 37.2 with 512), blocks of 512, one per SM, on the 2048^2 /
+  // 250k-node pair (114 against 140 with 256: fewer blocks make the grid
+  // barrier cheaper).  The 64-register variant (team_blocks_per_sm = 2) was
+  // slower on both (its spills and the larger grid), so it is opt-in.
+  h->block = o.block_size ? o.block_size
+                          : ((int64_t)(h->nV + 255) / 256 > h->num_sms ? 512 : 256);
+  h->minb = o.team_blocks_per_sm ? o.team_blocks_per_sm : 1;
   int per_sm = 0;
-  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, &per_sm), "occupancy");
+  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, h->minb, &per_sm), "occupancy");
   if (per_sm < 1) return fail(MREG_ERR_INVALID_ARG, "block_size %d does not fit on an SM", h->block);
   const int max_grid = per_sm * h->num_sms;
   const int want = (h->nV + h->block - 1) / h->block;
@@ -736,7 +746,7 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
       CK(mreg::launch_cluster(h->form, h->grad, a, h->cl_size, (cudaStream_t)stream),
          "cluster iteration kernel launch");
     } else {
-      CK(mreg::launch_iterate(h->form, h->grad, a, h->grid, h->block, (cudaStream_t)stream),
+      CK(mreg::launch_iterate(h->form, h->grad, h->minb, a, h->grid, h->block, (cudaStream_t)stream),
          "iteration kernel launch");
     }
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration

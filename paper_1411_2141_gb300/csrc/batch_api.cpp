@@ -247,8 +247,6 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   if (o.team_ctas != 0 && o.team_ctas != 1 && o.team_ctas != 2 && o.team_ctas != 4 &&
       o.team_ctas != 8)
     return fail(MREG_ERR_INVALID_ARG, "team_ctas must be 0, 1, 2, 4 or 8");
-  if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
-    return fail(MREG_ERR_INVALID_ARG, "team_blocks_per_sm must be 0, 1 or 2");
 
   // host topology of every pair, built on worker threads (pairs are
   // independent); the first failing pair (lowest index) is reported

@@ -18,8 +18,11 @@ struct GridTeam {
   __device__ __forceinline__ bool sync() { return gb.sync(s_flag); }
 };
 
-template <int GRAD>
-__global__ void __launch_bounds__(kIterBlockMax, 1) k_explicit(const IterArgs a) {
+// MINB: blocks per SM the register budget is sized for (1: up to 128
+// registers per thread; 2: up to 64 for 512-thread blocks, the rest in local
+// memory), picked by the host from the mesh size.
+template <int GRAD, int MINB>
+__global__ void __launch_bounds__(kIterBlockMax, MINB) k_explicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
   GridTeam team{GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull}, &s_flag,
@@ -27,8 +30,8 @@ __global__ void __launch_bounds__(kIterBlockMax, 1) k_explicit(const IterArgs a)
   run_explicit<GRAD>(a, team, dsm);
 }
 
-template <int FORM, int GRAD>
-__global__ void __launch_bounds__(kIterBlockMax, 1) k_implicit(const IterArgs a) {
+template <int FORM, int GRAD, int MINB>
+__global__ void __launch_bounds__(kIterBlockMax, MINB) k_implicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
   GridTeam team{GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull}, &s_flag,
@@ -54,23 +57,28 @@ __global__ void k_energy_final(const float2* __restrict__ epart, int ewarps, int
   }
 }
 
-void* select_kernel(int form, int grad) {
+template <int MINB>
+void* select_kernel_m(int form, int grad) {
   switch (form * 2 + (grad ? 1 : 0)) {
-    case 0: return (void*)k_explicit<0>;
-    case 1: return (void*)k_explicit<1>;
-    case 2: return (void*)k_implicit<kFormUmbrella, 0>;
-    case 3: return (void*)k_implicit<kFormUmbrella, 1>;
-    case 4: return (void*)k_implicit<kFormFemNodes, 0>;
-    case 5: return (void*)k_implicit<kFormFemNodes, 1>;
-    case 7: return (void*)k_implicit<kFormFemEdges, 1>;
+    case 0: return (void*)k_explicit<0, MINB>;
+    case 1: return (void*)k_explicit<1, MINB>;
+    case 2: return (void*)k_implicit<kFormUmbrella, 0, MINB>;
+    case 3: return (void*)k_implicit<kFormUmbrella, 1, MINB>;
+    case 4: return (void*)k_implicit<kFormFemNodes, 0, MINB>;
+    case 5: return (void*)k_implicit<kFormFemNodes, 1, MINB>;
+    case 7: return (void*)k_implicit<kFormFemEdges, 1, MINB>;
     default: return nullptr;
   }
 }
 
+void* select_kernel(int form, int grad, int minb) {
+  return minb == 2 ? select_kernel_m<2>(form, grad) : select_kernel_m<1>(form, grad);
+}
+
 }  // namespace
 
-cudaError_t iterate_max_blocks(int form, int grad, int block, int* max_blocks_per_sm) {
-  void* k = select_kernel(form, grad);
+cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max_blocks_per_sm) {
+  void* k = select_kernel(form, grad, minb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -78,9 +86,9 @@ cudaError_t iterate_max_blocks(int form, int grad, int block, int* max_blocks_pe
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k, block, smem);
 }
 
-cudaError_t launch_iterate(int form, int grad, const IterArgs& a, int grid, int block,
+cudaError_t launch_iterate(int form, int grad, int minb, const IterArgs& a, int grid, int block,
                            cudaStream_t s) {
-  void* k = select_kernel(form, grad);
+  void* k = select_kernel(form, grad, minb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
