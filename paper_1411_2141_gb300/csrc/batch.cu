@@ -213,14 +213,24 @@ constexpr int kWarpThreads = 256;
 __global__ void __launch_bounds__(kWarpThreads) k_batch_warp(const BatchWarpArgs b) {
   __shared__ float s_red[kMaxWarps * kRec];
   const int2 tile = __ldg(b.tiles + blockIdx.x);
-  const WarpArgs& a = b.pairs[tile.x];
+  const WarpArgs a = b.pairs[tile.x];   // the batched warp writes no image
   const int64_t n = (int64_t)a.W * a.H;
   const int64_t p1 = min(n, (int64_t)tile.y + kBatchTilePx);
+  const int64_t stride = blockDim.x;
   ff acc = ff_zero();
-  for (int64_t p = tile.y + threadIdx.x; p < p1; p += blockDim.x) {
+  int64_t p = tile.y + threadIdx.x;
+  for (; p + 3 * stride < p1; p += 4 * stride) {   // four pixels' load chains at once
+    float R[4], d[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ok[u] = warp_pixel(a, p + u * stride, R[u], d[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) acc = ff_add(acc, ff_prod(d[u], d[u]));
+  }
+  for (; p < p1; p += stride) {
     float R, d;
     if (!warp_pixel(a, p, R, d)) continue;
-    if (a.out) a.out[p] = R;
     acc = ff_add(acc, ff_prod(d, d));
   }
   float none[1] = {0.0f};

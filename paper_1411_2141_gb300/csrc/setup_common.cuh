@@ -38,6 +38,7 @@ constexpr int kWin = kSegLen + 2 * kWarm;
 constexpr int kPitch = 33;                 // 32 lines + 1 pad word
 constexpr int kWarpsPerBlock = 4;
 constexpr size_t kSmemPerWarp = (size_t)kWin * kPitch * sizeof(float);
+static_assert(kWin <= 4 * 32, "the row-pass staging loads at most 4 x 32 samples per line");
 
 
 // Exact causal initial value c+(0) = sum_k z1^k c~(k) over the mirror-periodic
@@ -93,9 +94,29 @@ __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int
 
   // stage the window: tile[k * kPitch + l] = gain * sample k of line l
   if (DIR == 0) {
-    for (int l = 0; l < nl; ++l) {
-      const float* src = in + (int64_t)(line0 + l) * in_stride + w0;
-      for (int k = lane; k < wn; k += 32) tile[k * kPitch + l] = gain * src[k];
+    // eight lines per round, every load of the round issued before the
+    // shared-memory stores (kWin <= 4 * 32 samples per line)
+    for (int l0 = 0; l0 < nl; l0 += 8) {
+      float v[8][4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = l0 + q;
+        const float* src = in + (int64_t)(line0 + (l < nl ? l : 0)) * in_stride + w0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = lane + 32 * j;
+          v[q][j] = (l < nl && k < wn) ? src[k] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = l0 + q;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = lane + 32 * j;
+          if (l < nl && k < wn) tile[k * kPitch + l] = gain * v[q][j];
+        }
+      }
     }
   } else {
     if (lane < nl) {

@@ -20,43 +20,74 @@ namespace {
 
 constexpr int kScanBlock = 1024;
 
-// Exclusive prefix sum of in[0..n) into out[0..n]; one block, chunk by chunk.
-__global__ void __launch_bounds__(kScanBlock) k_scan(const int* __restrict__ in, int n,
-                                                      int* __restrict__ out) {
-  __shared__ int s_warp[kScanBlock / 32];
-  __shared__ int s_carry;
+// Block-wide inclusive scan of one value per thread (warp shuffles, then the
+// warp totals); returns the thread's inclusive prefix, *total the block sum.
+__device__ __forceinline__ int block_incl_scan(int v, int* s_warp, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
+  int x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
   __syncthreads();
-  for (int base = 0; base < n; base += kScanBlock) {
-    const int i = base + threadIdx.x;
-    const int v = i < n ? in[i] : 0;
-    int x = v;
+  if (warp == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, off);
-      if (lane >= off) x += y;
+      const int y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      int w = s_warp[lane];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, off);
-        if (lane >= off) w += y;
-      }
-      s_warp[lane] = w;   // inclusive over warps
-    }
-    __syncthreads();
-    const int incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const int incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+  *total = s_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return incl;
+}
+
+// Exclusive prefix sum of in[0..n) into out[0..n] in three passes: block
+// sums, their scan (one block), and each block's scan plus its offset.
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(const int* __restrict__ in, int n,
+                                                           int* __restrict__ sums) {
+  __shared__ int s_warp[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  int total;
+  block_incl_scan(i < n ? in[i] : 0, s_warp, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_offsets(int* __restrict__ sums, int nb) {
+  __shared__ int s_warp[32];
+  __shared__ int s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += kScanBlock) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? sums[i] : 0;
+    int total;
+    const int incl = block_incl_scan(v, s_warp, &total);
     const int carry = s_carry;
-    if (i < n) out[i] = carry + incl - v;
+    if (i < nb) sums[i] = carry + incl - v;   // exclusive
     __syncthreads();
-    if (threadIdx.x == kScanBlock - 1) s_carry = carry + incl;
+    if (threadIdx.x == 0) s_carry = carry + total;
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[n] = s_carry;
+  if (threadIdx.x == 0) sums[nb] = s_carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(const int* __restrict__ in, int n,
+                                                            const int* __restrict__ sums,
+                                                            int* __restrict__ out) {
+  __shared__ int s_warp[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  const int v = i < n ? in[i] : 0;
+  int total;
+  const int incl = block_incl_scan(v, s_warp, &total);
+  if (i < n) out[i] = sums[blockIdx.x] + incl - v;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
 }
 
 __global__ void k_count_corners(const int* __restrict__ tri, int nT, int* __restrict__ cnt) {
@@ -280,9 +311,20 @@ namespace {
 size_t up8(size_t x) { return (x + 7) & ~(size_t)7; }
 }  // namespace
 
+int scan_blocks(int n) { return (n + kScanBlock - 1) / kScanBlock; }
+
+// out[0..n] = exclusive prefix sums of in[0..n) (sums: scan_blocks(n) + 1 ints)
+void scan(const int* in, int n, int* out, int* sums, cudaStream_t s) {
+  const int nb = scan_blocks(n) > 0 ? scan_blocks(n) : 1;
+  k_scan_sums<<<nb, kScanBlock, 0, s>>>(in, n, sums);
+  k_scan_offsets<<<1, kScanBlock, 0, s>>>(sums, nb);
+  k_scan_apply<<<nb, kScanBlock, 0, s>>>(in, n, sums, out);
+}
+
 size_t topology_scratch_bytes(int nV, int nT) {
   const size_t cap = 6 * (size_t)nT;
-  return up8(sizeof(int) * (4 * ((size_t)nV + 1) + cap)) + 2 * sizeof(double) * cap;
+  return up8(sizeof(int) * (4 * ((size_t)nV + 1) + cap + scan_blocks(nV) + 2)) +
+         2 * sizeof(double) * cap;
 }
 
 cudaError_t build_topology(const TopoArgs& a, void* scratch, cudaStream_t s) {
@@ -293,7 +335,9 @@ cudaError_t build_topology(const TopoArgs& a, void* scratch, cudaStream_t s) {
   int* upper = fill + (nV + 1);
   int* eoff = upper + (nV + 1);
   int* cand = eoff + (nV + 1);
-  double* Mo = (double*)((char*)scratch + up8(sizeof(int) * (4 * ((size_t)nV + 1) + cap)));
+  int* sums = cand + cap;
+  double* Mo = (double*)((char*)scratch +
+                         up8(sizeof(int) * (4 * ((size_t)nV + 1) + cap + scan_blocks(nV) + 2)));
   double* Ko = Mo + cap;
   const bool fem = a.form == kFormFemNodes || a.form == kFormFemEdges;
   cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(int) * (nV + 1), s);
@@ -305,13 +349,13 @@ cudaError_t build_topology(const TopoArgs& a, void* scratch, cudaStream_t s) {
   e = cudaMemsetAsync(a.flags, 0, 4 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_count_corners<<<grid_of(nT, 256), 256, 0, s>>>(a.tri, nT, cnt);
-  k_scan<<<1, kScanBlock, 0, s>>>(cnt, nV, a.inc_ptr);
+  scan(cnt, nV, a.inc_ptr, sums, s);
   k_fill_incidences<<<grid_of(nT, 256), 256, 0, s>>>(a.tri, nT, a.inc_ptr, fill, a.inc_tri);
   k_sort_incidences<<<grid_of(nV, 128), 128, 0, s>>>(a.tri, nV, a.inc_ptr, a.inc_tri, a.inc_opp,
                                                       cand, cnt, a.flags);
-  k_scan<<<1, kScanBlock, 0, s>>>(cnt, nV, a.adj_ptr);
+  scan(cnt, nV, a.adj_ptr, sums, s);
   k_fill_rows<<<grid_of(nV, 128), 128, 0, s>>>(nV, a.inc_ptr, cand, a.adj_ptr, a.adj_col, upper);
-  k_scan<<<1, kScanBlock, 0, s>>>(upper, nV, eoff);
+  scan(upper, nV, eoff, sums, s);
   k_edge_ids_upper<<<grid_of(nV, 128), 128, 0, s>>>(nV, a.adj_ptr, a.adj_col, eoff, a.adj_edge,
                                                      a.edges);
   k_edge_ids_lower<<<grid_of(nV, 128), 128, 0, s>>>(nV, a.adj_ptr, a.adj_col, a.adj_edge);

@@ -43,16 +43,39 @@ __global__ void k_count_equal(const int* __restrict__ p, int64_t n, int v, int* 
 
 constexpr int kWarpBlock = 256;
 
+// The image is walked in 32 x 32 pixel tiles (grid-stride over tiles); in a
+// 256-thread block, thread (x, r) takes the pixels (x, r + 8u), u = 0..3, of
+// its tile.  Neighbouring pixels share spline taps, corners and node
+// displacements, which the 2-D tile keeps in L1, and the four pixels' load
+// chains (owner -> corners -> displacements -> 16 taps) are issued together.
+// OUT: also write R (a separate instance, so that the MSD-only loop has no
+// stores for the compiler to order loads against).
+constexpr int kWarpTile = 32;
+static_assert(kWarpBlock == kWarpTile * 8, "one tile row per 32 threads, 8 rows per pass");
+
+template <bool OUT>
 __global__ void __launch_bounds__(kWarpBlock) k_warp_msd(const WarpArgs a) {
   __shared__ float s_red[kMaxWarps * kRec];
-  const int64_t n = (int64_t)a.W * a.H;
+  const int W = a.W, H = a.H;
+  const int tx = (W + kWarpTile - 1) / kWarpTile, ty = (H + kWarpTile - 1) / kWarpTile;
+  const int ntiles = tx * ty;
   ff acc = ff_zero();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    float R, d;
-    if (!warp_pixel(a, p, R, d)) continue;
-    if (a.out) a.out[p] = R;
-    acc = ff_add(acc, ff_prod(d, d));
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x = (tile % tx) * kWarpTile + (threadIdx.x & 31);
+    const int y0 = (tile / tx) * kWarpTile + (threadIdx.x >> 5);
+    float R[4], d[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int y = y0 + 8 * u;
+      ok[u] = x < W && y < H && warp_pixel(a, (int64_t)y * W + x, R[u], d[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!ok[u]) continue;
+      if (OUT) a.out[(int64_t)(y0 + 8 * u) * W + x] = R[u];
+      acc = ff_add(acc, ff_prod(d[u], d[u]));
+    }
   }
   float none[1] = {0.0f};
   block_reduce_store<1, true>(none, acc, a.part + (size_t)blockIdx.x * kRec, s_red);
@@ -233,8 +256,7 @@ cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tp
 }
 
 int warp_grid_blocks(int W, int H, int num_sms) {
-  const int64_t n = (int64_t)W * H;
-  const int64_t need = (n + kWarpBlock - 1) / kWarpBlock;
+  const int64_t need = (int64_t)((W + kWarpTile - 1) / kWarpTile) * ((H + kWarpTile - 1) / kWarpTile);
   const int64_t cap = (int64_t)num_sms * 8;
   return (int)(need < cap ? need : cap);
 }
@@ -252,7 +274,8 @@ cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int
 
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
                             cudaStream_t s) {
-  k_warp_msd<<<grid, kWarpBlock, 0, s>>>(a);
+  if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a);
+  else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a);
   if (msd_out) k_msd_final<<<1, 32, 0, s>>>(a.part, grid, inv_count, msd_out);
   return cudaGetLastError();
 }
