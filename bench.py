@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--team", default=None,
                    help="config 3: fixed team shape 'ctas,block[,blocks_per_sm]' instead of "
                         "the autotuner")
+    p.add_argument("--teams", type=int, default=0,
+                   help="config 3 with --team: number of teams (0 = as many as are co-resident)")
     p.add_argument("--pairs", type=int, default=0,
                    help="config 3: only the first N pairs of the batch (small profiling case)")
     p.add_argument("--single", action="store_true",
@@ -157,6 +159,8 @@ def run_reference(args, rank, world):
         return
     if args.config == 3:
         return run_reference_batch(args)
+    if args.config == 4:
+        return run_reference_adjoint(args)
     spec = inputs.config_spec(args.config)
     case = inputs.make_case(spec)
     for _ in range(args.warmup):
@@ -190,6 +194,35 @@ def launches_per_registration(args, n_iter: int) -> int:
     1024-iteration chunk, warp + MSD and the final MSD sum."""
     chunks = (n_iter + 1023) // 1024
     return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 2)
+
+
+def run_reference_adjoint(args):
+    from oracle import adjoint, register
+    cases = adjoint_cases(args.pairs)
+    K = cases[0].spec.n_iter
+    total, n = 0.0, 0
+    for step in range(args.warmup + args.steps):
+        c = cases[step % len(cases)]
+        t0 = time.perf_counter()
+        pb = register.Problem(c.V, c.T, c.Re, c.Te, c.spec.alpha, c.spec.tau, "S0", "G1")
+        adjoint.unrolled_grad(pb, _smooth_u0(c).astype(np.float64), K)
+        if step >= args.warmup:
+            total += time.perf_counter() - t0
+            n += 1
+    value = n / total
+    line = {
+        "impl": "reference", "metric": "unrolled gradients/s", "value": value,
+        "unit": "gradients/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"config4: pairs of 256x256, gradient through {K} iterations",
+                   "pairs": len(cases), "iterations": K},
+        "cpu_baseline": {"value": value, "unit": "gradients/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: one pair's set-up, forward iterations and adjoint"},
+        "e2e": {"value": value, "unit": "gradients/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_reference_batch(args):
@@ -545,7 +578,7 @@ def run_ours_batch(args, rank, world, local_rank):
         b.close()
         b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
                        grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
-                       team_blocks_per_sm=per_sm, stream=stream)
+                       team_blocks_per_sm=per_sm, grid_blocks=args.teams, stream=stream)
         tune_s, tune_ms = 0.0, {}
     else:
         t0 = time.perf_counter()
@@ -660,6 +693,98 @@ def run_ours_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     b.close()
 
+# ------------------------------------------------- differentiation form
+def adjoint_cases(n_pairs: int = 0):
+    return inputs.make_cases(inputs.batched_specs(4, n_pairs or None))
+
+
+def _smooth_u0(c):
+    x = c.V[:, 0].astype(np.float64)
+    y = c.V[:, 1].astype(np.float64)
+    s = c.spec.side
+    return np.stack([np.sin(2 * np.pi * x / s), np.cos(2 * np.pi * y / s)], axis=1).astype(np.float32)
+
+
+def run_ours_adjoint(args, rank, world, local_rank):
+    """One step = the gradient of the warp energy after a 20-iteration
+    unrolled registration (explicit form, spline gradient) with respect to
+    the starting displacement, for each of the 64 pairs: 20 forward
+    iterations with every state kept, the warp energy and its adjoint, and
+    20 adjoint steps."""
+    import torch
+    from paper_1411_2141_gb300 import mreg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    mreg.load()
+    cases = adjoint_cases(args.pairs)
+    K = cases[0].spec.n_iter
+    stream = torch.cuda.current_stream()
+    regs = [mreg.Registration(c.V, c.T, torch.from_numpy(c.Re).to(dev), torch.from_numpy(c.Te).to(dev),
+                              c.spec.alpha, c.spec.tau, mode="S0", grad="G1", stream=stream)
+            for c in cases]
+    u0 = [torch.from_numpy(_smooth_u0(c)).to(dev) for c in cases]
+    E = torch.empty(len(cases), dtype=torch.float64, device=dev)
+    g = [torch.empty_like(u) for u in u0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        for k, r in enumerate(regs):
+            r.unroll_grad(u0[k], K, E[k:k + 1], g[k], stream)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        one_step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_s = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, world, dev)
+    if rank != 0:
+        return
+    value = whole_job_rate(args.steps * len(cases), world, total_s)
+    line = {
+        "metric": "unrolled gradients/s", "value": value, "unit": "gradients/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"config4: {len(cases)} pairs of 256x256, {cases[0].n_nodes}-node "
+                               f"meshes, gradient of the warp energy through {K} explicit "
+                               f"iterations (spline gradient) with respect to u0",
+                   "pairs": len(cases), "iterations": K,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{args.gpus}"},
+        "energy_mean": float(E.mean().item()), "clocks": clk,
+        "gpu_launches": len(cases) * (2 * K + 4 + K) * args.steps,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import adjoint, register
+        c = cases[0]
+        t0 = time.perf_counter()
+        pb = register.Problem(c.V, c.T, c.Re, c.Te, c.spec.alpha, c.spec.tau, "S0", "G1")
+        adjoint.unrolled_grad(pb, _smooth_u0(c).astype(np.float64), K)
+        t1 = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / t1, "unit": "gradients/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "one pair: set-up, 20 forward iterations and the adjoint "
+                                          "recursion, numpy/scipy FP64, 1 thread"}
+    print(json.dumps(line), flush=True)
+    for r in regs:
+        r.close()
+
+
 
 def main():
     args = parse()
@@ -674,7 +799,9 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        if args.config == 3 and args.single:
+        if args.config == 4:
+            run_ours_adjoint(args, rank, world, local_rank)
+        elif args.config == 3 and args.single:
             run_ours_batch_single(args, rank, world, local_rank)
         elif args.config == 3:
             run_ours_batch(args, rank, world, local_rank)

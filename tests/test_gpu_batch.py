@@ -198,3 +198,33 @@ def test_batched_workload_full_size(mreg):
         assert np.isfinite(msd).all() and (msd < before).all()
         for k in range(len(cases)):
             b.stats(k)
+
+
+def _ragged_case(H, W, seed):
+    """A small H x W pair (any aspect ratio) with a regular mesh of its
+    corners and a few interior nodes."""
+    from tests.test_gpu_parity import _ragged_case as make
+    return make(H, W, seed)
+
+
+def test_batch_with_degenerate_and_ragged_pairs(mreg, small):
+    """A 2x2 pair (two triangles), a ragged non-square pair and normal pairs in
+    one batch, every form; and a batch of a single pair."""
+    tiny = _ragged_case(2, 2, seed=1)
+    ragged = _ragged_case(37, 70, seed=2)
+    cases = [small[0], tiny, ragged, small[2]]
+    n = 6
+    for mode, grad in (("S0", "G0"), ("S1", "G0"), ("S2", "G1")):
+        with mreg.Batch([(c.V, c.T, c.Re, c.Te) for c in cases], 0.1, 1.0, mode=mode,
+                        grad=grad) as b:
+            b.run(n)
+            msd = b.msd()
+            for k, c in enumerate(cases):
+                pb = register.Problem(c.V, c.T, c.Re, c.Te, 0.1, 1.0, mode, grad)
+                u_ref, _ = pb.run(n)
+                m_ref = pb.msd(u_ref)
+                assert np.abs(b.get_u(k) - u_ref).max() <= U_TOL
+                assert abs(msd[k] - m_ref) <= MSD_RTOL * max(m_ref, 1e-12)
+    with mreg.Batch([(tiny.V, tiny.T, tiny.Re, tiny.Te)], 0.1, 1.0, mode="S1") as b:
+        b.run(3)
+        assert b.shape()[3] == 1 and np.isfinite(b.msd()).all()
