@@ -289,9 +289,10 @@ PROFILE_C3 = ("k_batch_256_uneven_pairs.md",
                "setup_common.cuh", "mreg_internal.h"])
 
 
-def profiled_traffic(profile):
+def profiled_traffic(profile, shape=None):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's sources changed since the capture (or no full-size capture)."""
+    kernel's sources changed since the capture, the summary has no full-size
+    capture, or (batched form) the launch's team shape is not the profiled one."""
     import hashlib
     import re
     name, sources = profile
@@ -303,6 +304,10 @@ def profiled_traffic(profile):
     m_bytes = re.search(r"DRAM bytes per launch: (\d+)", text)
     if not (m_hash and m_bytes):
         return None
+    if shape is not None:
+        m_shape = re.search(r"team shape \(ctas,block,blocks_per_sm\): (\d+),(\d+),(\d+)", text)
+        if not m_shape or tuple(int(x) for x in m_shape.groups()) != tuple(shape):
+            return None
     h = hashlib.sha256()
     for f in sources:
         with open(os.path.join(ROOT, "paper_1411_2141_gb300", "csrc", f), "rb") as fh:
@@ -677,7 +682,9 @@ def run_ours_batch(args, rank, world, local_rank):
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": per_iter_total * n_iter,
-                     "traffic": profiled_traffic(PROFILE_C3) if not args.pairs else None},
+                     "traffic": (profiled_traffic(PROFILE_C3, (ctas, block, per_sm))
+                                 if not args.pairs and (args.mode, args.grad, args.coeff)
+                                 == ("S1", "G0", "fp32") else None)},
         "clocks": clk,
         "gpu_launches": BATCH_LAUNCHES * args.steps,
     }

@@ -13,9 +13,9 @@
  *       gradient of Eq. 9-10 on the deformed mesh, or the analytic B-spline
  *       gradient; atomics-free, node-centric assembly
  *   a3  the update: explicit step + one umbrella smoothing pass (Eq. 5, 14),
- *       or a semi-implicit step whose sparse SPD system (abstract: "a sparse
- *       system of linear equations") is solved by Jacobi-preconditioned CG
- *       to a stated FP64 residual
+ *       or a semi-implicit step whose sparse SPD system (the abstract's
+ *       linear system) is solved by Jacobi-preconditioned CG to a stated
+ *       residual formed in extended precision
  *   a4  the dense barycentric warp of the template and the MSD (Sec. 1,
  *       Fig. 3, Table 1)
  *
