@@ -131,3 +131,38 @@ def test_batch_host_validation_errors(lib):
                                  C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
     assert lib.mreg_batch_run(None, 1, None) == mreg.MREG_ERR_INVALID_ARG
     lib.mreg_batch_destroy(None)
+
+
+def test_option_validation_of_the_newer_fields(lib):
+    V, T = _mesh_square()
+    img = np.zeros((6, 8), np.float32)
+    E = mreg
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, smooth_passes=-1))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, smooth_passes=65))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S1", smooth_passes=2))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, team_blocks_per_sm=3))
+    o = mreg.make_options(host_topology=True)
+    assert o.host_topology == 1
+    o.host_topology = 2
+    h = C.c_void_p()
+    im = mreg._image(img, [])
+    mesh = mreg.mreg_mesh(4, 2, V.ctypes.data_as(C.POINTER(C.c_float)),
+                          T.ctypes.data_as(C.POINTER(C.c_int32)))
+    assert lib.mreg_create(C.byref(mesh), C.byref(im), C.byref(im), 0.1, 1.0, C.byref(o), None,
+                           C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
+    o = mreg.make_options(coeff_bf16=True)
+    o.coeff_bf16 = 3
+    assert lib.mreg_create(C.byref(mesh), C.byref(im), C.byref(im), 0.1, 1.0, C.byref(o), None,
+                           C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
+    assert lib.mreg_warp_energy_grad(None, None, None, None, None) == mreg.MREG_ERR_INVALID_ARG
+    assert lib.mreg_unroll_grad(None, None, 3, None, None, None) == mreg.MREG_ERR_INVALID_ARG
+
+
+def test_options_struct_matches_the_header():
+    """Every mreg_options field of the header is in the binding's struct, in order."""
+    import re
+    text = open(os.path.join(ROOT, "include", "mreg.h")).read()
+    body = text[text.index("typedef struct {\n  int32_t mode;"):text.index("} mreg_options;")]
+    names = re.findall(r"^\s*(?:int32_t|double)\s+(\w+);", body, flags=re.M)
+    assert [n if n != "lambda" else "lambda_" for n in names] == \
+        [f for f, _ in mreg.mreg_options._fields_]

@@ -188,3 +188,18 @@ def test_unrolled_gradient_with_repeated_smoothing(mreg, case0):
         r.unroll_grad(torch.from_numpy(u0).cuda(), 10, None, g)
         g = g.cpu().numpy()
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+
+
+def test_unroll_of_zero_iterations_is_the_warp_gradient(mreg, case0):
+    u0 = torch.from_numpy(_smooth_u(case0, 0.5, 14)).cuda()
+    with mreg.Registration(case0.V, case0.T, case0.Re, case0.Te, 0.1, 1.0, mode="S0",
+                           grad="G1") as r:
+        g0 = torch.empty_like(u0)
+        g1 = torch.empty_like(u0)
+        E0 = torch.empty(1, dtype=torch.float64, device="cuda")
+        E1 = torch.empty_like(E0)
+        r.unroll_grad(u0, 0, E0, g0)
+        r.warp_energy_grad(u0, E1, g1)
+        torch.cuda.synchronize()
+        assert torch.equal(g0, g1) and torch.equal(E0, E1)
+        assert np.abs(r.get_u() - u0.cpu().numpy()).max() == 0.0   # the iterate is u0

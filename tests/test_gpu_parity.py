@@ -391,3 +391,27 @@ def test_device_precomputation_rejects_a_node_outside_every_triangle(mreg, c0):
     V = np.concatenate([c0.V, [[5.5, 7.25]]]).astype(np.float32)   # unused extra node
     with pytest.raises(mreg.MregError, match="no triangle"):
         mreg.Registration(V, c0.T, c0.Re, c0.Te, 0.1, 1.0)
+
+
+@pytest.mark.parametrize("mode", ["S0", "S1"])
+def test_run_longer_than_one_launch(mreg, mode):
+    """1100 iterations: the iteration kernel is launched in chunks of 1024,
+    so the state, the force buffers and the histories cross a launch."""
+    case = _ragged_case(24, 25, seed=3)
+    n = 1100
+    pb = _oracle(case, mode)
+    u_ref, e_ref = pb.run(n)
+    with _reg(mreg, case, mode) as r:
+        r.step(n)
+        u = r.get_u()
+        e = r.get_field(mreg.MREG_FIELD_ENERGY)
+        F = r.get_field(mreg.MREG_FIELD_FORCE)
+        r.stats()
+    assert len(e) == n
+    assert np.abs(u - u_ref).max() <= U_TOL
+    np.testing.assert_allclose(e, e_ref, rtol=1e-5, atol=1e-12)
+    # the force the last iteration applied: F at u_{n-1}
+    u_prev, _ = pb.run(n - 1)
+    f, rr, g = pb.sample(u_prev)
+    F_ref = pb.force(u_prev, f, rr, g)
+    assert np.abs(F - F_ref).max() <= 1e-4 * max(np.abs(F_ref).max(), 1e-6)
