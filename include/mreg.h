@@ -143,10 +143,11 @@ typedef struct {
                           error this adds is stated against the FP64 method,
                           not bounded by the FP32 tolerances.  (default 0)  */
   int32_t team_ctas;   /* batched engine only: CTAs per team (one thread-block
-                          cluster registers one pair at a time): 1, 2, 4 or
-                          8; 0 = 4.  block_size is the team CTAs' size there
-                          (0 = 512) and grid_blocks the number of teams (0 =
-                          as many as are co-resident, at most one per pair). */
+                          cluster registers one pair at a time): 1, 2, 4, 8
+                          or 16 (16 is a non-portable cluster size); 0 = 4.
+                          block_size is the team CTAs' size there (0 = 512)
+                          and grid_blocks the number of teams (0 = as many
+                          as are co-resident, at most one per pair).        */
   int32_t smooth_passes; /* explicit mode: Eq. 14 passes per iteration (the
                           paper applies one and notes that more give a
                           smoother field); 0 = 1, at most 64; other modes
@@ -369,10 +370,10 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
 mreg_status mreg_batch_run(mreg_batch* b, int32_t n_iters, void* stream);
 
 /* Autotuner: times mreg_batch_run(n_iters) for every supported team shape
- * (team_ctas in 1, 2, 4, 8 x block_size in 128, 256, 512 x blocks_per_sm in
- * 1, 2, skipping shapes that do not fit), keeps the fastest for later runs
- * and returns it.  Each shape is run once to warm up and timed on the best
- * of two runs with CUDA events.  times_ms (may be NULL) receives 24 entries,
+ * (team_ctas in 1, 2, 4, 8, 16 x block_size in 128, 256, 512 x blocks_per_sm
+ * in 1, 2, skipping shapes that do not fit or launch), keeps the fastest for
+ * later runs and returns it.  Each shape is run once to warm up and timed on
+ * the best of two runs with CUDA events.  times_ms (may be NULL) receives 30 entries,
  * row-major over (team_ctas, block_size, blocks_per_sm), -1 for skipped
  * shapes.  Blocks.  Outputs may be NULL.                                    */
 mreg_status mreg_batch_tune(mreg_batch* b, int32_t n_iters, void* stream, int32_t* team_ctas,

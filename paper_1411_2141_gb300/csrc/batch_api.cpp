@@ -25,7 +25,7 @@ using namespace mreg::host;   // NOLINT
 namespace {
 
 constexpr int kBatchHist = 1024;   // per-pair history entries (energy, CG)
-constexpr int kShapesCtas[4] = {1, 2, 4, 8};
+constexpr int kShapesCtas[5] = {1, 2, 4, 8, 16};   // 16: a non-portable cluster size
 constexpr int kShapesBlock[3] = {128, 256, 512};
 constexpr int kShapesMinb[2] = {1, 2};
 
@@ -245,8 +245,8 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   mreg_status st = validate_options(o, alpha, tau, &lam);
   if (st) return st;
   if (o.team_ctas != 0 && o.team_ctas != 1 && o.team_ctas != 2 && o.team_ctas != 4 &&
-      o.team_ctas != 8)
-    return fail(MREG_ERR_INVALID_ARG, "team_ctas must be 0, 1, 2, 4 or 8");
+      o.team_ctas != 8 && o.team_ctas != 16)
+    return fail(MREG_ERR_INVALID_ARG, "team_ctas must be 0, 1, 2, 4, 8 or 16");
 
   // host topology of every pair, built on worker threads (pairs are
   // independent); the first failing pair (lowest index) is reported
@@ -632,7 +632,7 @@ mreg_status mreg_batch_tune(mreg_batch* b, int32_t n_iters, void* stream, int32_
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
   mreg_status st = MREG_OK;
-  for (int ci = 0; ci < 4 && !st; ++ci)
+  for (int ci = 0; ci < 5 && !st; ++ci)
     for (int ki = 0; ki < 3 && !st; ++ki)
       for (int mi = 0; mi < 2 && !st; ++mi) {
         float t = -1.0f;

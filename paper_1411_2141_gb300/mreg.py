@@ -462,11 +462,11 @@ class Batch:
         blocks_per_sm), times) with times[(ctas, block, per_sm)] in ms (None
         where the shape is skipped)."""
         c, k, m = C.c_int32(), C.c_int32(), C.c_int32()
-        t = (C.c_float * 24)()
+        t = (C.c_float * 30)()
         _check(load().mreg_batch_tune(self._h, int(n_iters), _stream_ptr(stream), C.byref(c),
                                       C.byref(k), C.byref(m), t), "mreg_batch_tune")
         times = {}
-        for i, ctas in enumerate((1, 2, 4, 8)):
+        for i, ctas in enumerate((1, 2, 4, 8, 16)):
             for j, blk in enumerate((128, 256, 512)):
                 for q, per_sm in enumerate((1, 2)):
                     v = float(t[(i * 3 + j) * 2 + q])
