@@ -162,6 +162,18 @@ typedef struct {
                           sized for: 1 (up to 128 registers per thread) or 2
                           (up to 64, the rest in local memory); 0 = 1 (the
                           batched engine's autotuner tries both).           */
+  /* Device memory.  With alloc non-NULL every device buffer of the handle or
+   * batch comes from alloc(bytes, stream, alloc_ctx) -- stream being the
+   * stream of the call that allocates -- and goes back through
+   * free(ptr, stream, alloc_ctx), also from mreg_destroy /
+   * mreg_batch_destroy (stream NULL there).  alloc returns NULL on failure
+   * (reported as MREG_ERR_OOM) and 256-byte-aligned memory otherwise; a
+   * misaligned block is given back and reported as MREG_ERR_INVALID_ARG.
+   * NULL (default): cudaMalloc / cudaFree.  The caller keeps the callbacks
+   * and alloc_ctx valid until the handle is destroyed.                     */
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* alloc_ctx;
 } mreg_options;
 
 typedef struct {

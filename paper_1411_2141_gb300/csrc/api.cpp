@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -33,6 +34,32 @@ mreg_status fail(mreg_status st, const char* fmt, ...) {
   va_end(ap);
   g_last_error = buf;
   return st;
+}
+
+mreg_status DevMem::get(void** p, size_t bytes, void* stream) const {
+  *p = nullptr;
+  if (!alloc) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return cuda_fail(e, "device allocation");
+    }
+    return MREG_OK;
+  }
+  void* q = alloc(bytes, stream, ctx);
+  if (!q) return fail(MREG_ERR_OOM, "the caller's allocator returned NULL for %zu bytes", bytes);
+  if ((uintptr_t)q % 256 != 0) {
+    free(q, stream, ctx);
+    return fail(MREG_ERR_INVALID_ARG, "the caller's allocator returned memory not aligned to 256 bytes");
+  }
+  *p = q;
+  return MREG_OK;
+}
+
+void DevMem::put(void* p, void* stream) const {
+  if (!p) return;
+  if (alloc) free(p, stream, ctx);
+  else cudaFree(p);
 }
 
 mreg_status cuda_fail(cudaError_t e, const char* what) {
@@ -251,6 +278,7 @@ struct mreg_handle {
   int *tri = nullptr, *inc_ptr = nullptr;
   int2* inc_opp = nullptr;
   int* inc_tri = nullptr;      // incident triangle ids (same order as inc_opp)
+  DevMem mem;                  // the caller's allocator, or cudaMalloc / cudaFree
   void* adj_buf = nullptr;     // warp-energy adjoint scratch, allocated on first use
   void* unroll_buf = nullptr;  // unrolled-adjoint states and vectors, grown on demand
   size_t unroll_bytes = 0;
@@ -612,7 +640,11 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16),
                o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8),
                o_c16 = take(o.coeff_bf16 ? npx * 2 : 0);
-  CK(cudaMalloc(&h->arena, off), "device allocation");
+  h->mem.alloc = o.alloc;
+  h->mem.free = o.free;
+  h->mem.ctx = o.alloc_ctx;
+  st = h->mem.get(&h->arena, off, stream);
+  if (st) return st;
   char* base = (char*)h->arena;
   h->Re = (float*)(base + o_Re);
   h->Te = (float*)(base + o_Te);
@@ -671,7 +703,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   CK(up(h->tri, hm.tri.data(), nT * 12), "upload");
   if (dev_topo) {
     void* scratch = nullptr;
-    CK(cudaMalloc(&scratch, mreg::topology_scratch_bytes(h->nV, h->nT)), "device allocation");
+    st = h->mem.get(&scratch, mreg::topology_scratch_bytes(h->nV, h->nT), stream);
+    if (st) return st;
     mreg::TopoArgs ta{};
     ta.nV = h->nV;
     ta.nT = h->nT;
@@ -698,7 +731,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
     cudaError_t e = mreg::build_topology(ta, scratch, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, h->counters, sizeof flags, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(scratch);
+    h->mem.put(scratch, stream);
     CK(e, "device mesh pre-computation");
     if (flags[0]) return fail(MREG_ERR_BAD_MESH, "%d nodes belong to no triangle", flags[0]);
     h->nnz = flags[1];
@@ -762,8 +795,10 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   if (!energy_dev && !grad_dev) return MREG_OK;
   const size_t rg_bytes = align_up((size_t)h->W * h->H * sizeof(float2));
-  if (!h->adj_buf)
-    CK(cudaMalloc(&h->adj_buf, rg_bytes + 3 * (size_t)h->nT * sizeof(float2)), "device allocation");
+  if (!h->adj_buf) {
+    const mreg_status st = h->mem.get(&h->adj_buf, rg_bytes + 3 * (size_t)h->nT * sizeof(float2), stream);
+    if (st) return st;
+  }
   mreg::WarpArgs a{};
   a.W = h->W;
   a.H = h->H;
@@ -797,10 +832,11 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   const size_t need = vec * ((size_t)n_iters + 3);
   if (need > h->unroll_bytes) {
     CK(cudaStreamSynchronize(s), "synchronize");
-    if (h->unroll_buf) cudaFree(h->unroll_buf);
+    h->mem.put(h->unroll_buf, stream);
     h->unroll_buf = nullptr;
     h->unroll_bytes = 0;
-    CK(cudaMalloc(&h->unroll_buf, need), "device allocation");
+    const mreg_status st = h->mem.get(&h->unroll_buf, need, stream);
+    if (st) return st;
     h->unroll_bytes = need;
   }
   char* base = (char*)h->unroll_buf;
@@ -978,9 +1014,9 @@ void mreg_destroy(mreg_handle* h) {
   if (!h) return;
   if (h->arena || h->adj_buf || h->unroll_buf) {
     cudaSetDevice(h->dev);
-    if (h->arena) cudaFree(h->arena);
-    if (h->adj_buf) cudaFree(h->adj_buf);
-    if (h->unroll_buf) cudaFree(h->unroll_buf);
+    h->mem.put(h->arena, nullptr);
+    h->mem.put(h->adj_buf, nullptr);
+    h->mem.put(h->unroll_buf, nullptr);
   }
   delete h;
 }

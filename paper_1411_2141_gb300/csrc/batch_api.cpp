@@ -47,6 +47,7 @@ struct mreg_batch {
   std::vector<PairInfo> info;
   int64_t n_px = 0, n_nodes = 0, n_tris = 0, n_edges = 0, n_nnz = 0;
   void* arena = nullptr;
+  DevMem mem;   // the caller's allocator, or cudaMalloc / cudaFree
   // packed arrays (device)
   float *Re = nullptr, *Te = nullptr, *cTe = nullptr;
   __nv_bfloat16* cTe16 = nullptr;
@@ -103,10 +104,11 @@ mreg_status choose_shape(mreg_batch* b, int ctas, int block, int minb) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
-    if (b->part) cudaFree(b->part);
+    b->mem.put(b->part, nullptr);
     b->part = nullptr;
     b->part_bytes = 0;
-    CK(cudaMalloc(&b->part, need), "device allocation");
+    const mreg_status st = b->mem.get((void**)&b->part, need, nullptr);
+    if (st) return st;
     b->part_bytes = need;
   }
   b->team_ctas = ctas;
@@ -124,10 +126,11 @@ mreg_status ensure_epart(mreg_batch* b, int n_iters) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  if (b->epart) cudaFree(b->epart);
+  b->mem.put(b->epart, nullptr);
   b->epart = nullptr;
   b->epart_bytes = 0;
-  CK(cudaMalloc(&b->epart, need), "device allocation");
+  const mreg_status st = b->mem.get((void**)&b->epart, need, nullptr);
+  if (st) return st;
   b->epart_bytes = need;
   return MREG_OK;
 }
@@ -223,9 +226,9 @@ void mreg_batch_destroy(mreg_batch* b) {
   if (b->cap) cudaStreamDestroy(b->cap);
   for (cudaEvent_t e : b->ev_iter)
     if (e) cudaEventDestroy(e);
-  if (b->part) cudaFree(b->part);
-  if (b->epart) cudaFree(b->epart);
-  if (b->arena) cudaFree(b->arena);
+  b->mem.put(b->part, nullptr);
+  b->mem.put(b->epart, nullptr);
+  b->mem.put(b->arena, nullptr);
   delete b;
 }
 
@@ -398,7 +401,11 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
                o_to0 = take((P + 1) * 4), o_to1 = take((P + 1) * 4), o_no = take((P + 1) * 4),
                o_tro = take((P + 1) * 4), o_eo = take((P + 1) * 4), o_tiles = take(NTL * 8),
                o_tlo = take((P + 1) * 4), o_rec = take(NTL * mreg::kRec * 4);
-  CK(cudaMalloc(&b->arena, off), "device allocation");
+  b->mem.alloc = o.alloc;
+  b->mem.free = o.free;
+  b->mem.ctx = o.alloc_ctx;
+  st = b->mem.get(&b->arena, off, stream);
+  if (st) return st;
   char* base = (char*)b->arena;
   auto F32 = [&](size_t o2) { return (float*)(base + o2); };
   auto I32 = [&](size_t o2) { return (int*)(base + o2); };

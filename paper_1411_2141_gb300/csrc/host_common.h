@@ -48,6 +48,16 @@ mreg_status validate_image(const mreg_image* im, const char* name);
 mreg_status validate_options(const mreg_options& o, double alpha, double tau, double* lam);
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Device memory of one handle: the caller's allocator from mreg_options, or
+// cudaMalloc / cudaFree.
+struct DevMem {
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free)(void*, void*, void*) = nullptr;
+  void* ctx = nullptr;
+  mreg_status get(void** p, size_t bytes, void* stream) const;
+  void put(void* p, void* stream) const;
+};
+
 }  // namespace host
 }  // namespace mreg
 

@@ -72,13 +72,18 @@ class mreg_image(C.Structure):
                 ("data", C.c_void_p), ("on_device", C.c_int32)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
                 ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
                 ("smooth_passes", C.c_int32), ("host_topology", C.c_int32),
-                ("team_blocks_per_sm", C.c_int32)]
+                ("team_blocks_per_sm", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
 
 
 class mreg_stats_t(C.Structure):
@@ -206,7 +211,7 @@ def default_options() -> mreg_options:
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
                  coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0,
-                 smooth_passes=0, host_topology=False) -> mreg_options:
+                 smooth_passes=0, host_topology=False, allocator=None) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -225,7 +230,34 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.team_blocks_per_sm = int(team_blocks_per_sm)
     o.smooth_passes = int(smooth_passes)
     o.host_topology = int(bool(host_topology))
+    if allocator is not None:
+        o.alloc = allocator.alloc_fn
+        o.free = allocator.free_fn
     return o
+
+
+class TorchAllocator:
+    """Device memory for handles from PyTorch's caching allocator (pass as
+    ``allocator=`` to Registration or Batch).  Keep the object alive as long
+    as the handles that use it; the wrappers below hold a reference."""
+
+    def __init__(self):
+        import torch
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                s = torch.cuda.ExternalStream(stream) if stream else None
+                return torch.cuda.caching_allocator_alloc(int(nbytes), stream=s)
+            except Exception:   # reported to the library as an allocation failure
+                return None
+
+        def _free(ptr, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
 
 
 def _image(img, keep: list) -> mreg_image:
@@ -258,6 +290,7 @@ class Registration:
         lib = load()
         if options is None:
             options = make_options(**kw)
+        self._allocator = kw.get("allocator")   # callbacks must outlive the handle
         keep: list = []
         Vh = np.ascontiguousarray(V, dtype=np.float32)
         Th = np.ascontiguousarray(T, dtype=np.int32)
@@ -407,6 +440,7 @@ class Batch:
         lib = load()
         if options is None:
             options = make_options(**kw)
+        self._allocator = kw.get("allocator")   # callbacks must outlive the batch
         pairs = list(pairs)
         n = len(pairs)
         if n < 1:

@@ -163,6 +163,7 @@ def test_options_struct_matches_the_header():
     import re
     text = open(os.path.join(ROOT, "include", "mreg.h")).read()
     body = text[text.index("typedef struct {\n  int32_t mode;"):text.index("} mreg_options;")]
-    names = re.findall(r"^\s*(?:int32_t|double)\s+(\w+);", body, flags=re.M)
+    names = [m.group(1) or m.group(2) for m in re.finditer(
+        r"^\s*(?:(?:int32_t|double|void\*)\s+(\w+);|void\*?\s*\(\*(\w+)\))", body, flags=re.M)]
     assert [n if n != "lambda" else "lambda_" for n in names] == \
         [f for f, _ in mreg.mreg_options._fields_]

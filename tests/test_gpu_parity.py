@@ -415,3 +415,34 @@ def test_run_longer_than_one_launch(mreg, mode):
     f, rr, g = pb.sample(u_prev)
     F_ref = pb.force(u_prev, f, rr, g)
     assert np.abs(F - F_ref).max() <= 1e-4 * max(np.abs(F_ref).max(), 1e-6)
+
+
+def test_caller_allocator(mreg, c0):
+    """Every device buffer of a handle or batch can come from the caller's
+    allocator (here PyTorch's caching allocator) and goes back to it."""
+    alloc = mreg.TorchAllocator()
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    with _reg(mreg, c0, "S1", allocator=alloc) as r:
+        assert torch.cuda.memory_allocated() > base   # the arena is torch's memory
+        r.step(20)
+        u_a, m_a = r.get_u(), r.msd()
+        g_a = torch.empty(c0.n_nodes, 2, device="cuda")
+        r.warp_energy_grad(torch.from_numpy(u_a).cuda(), None, g_a)   # adjoint scratch too
+        torch.cuda.synchronize()
+        del g_a
+    with _reg(mreg, c0, "S1") as r:
+        r.step(20)
+        assert np.array_equal(u_a, r.get_u()) and m_a == r.msd()
+    with mreg.Batch([(c0.V, c0.T, c0.Re, c0.Te)] * 2, 0.1, 1.0, mode="S1", allocator=alloc) as b:
+        b.run(5)
+        assert np.isfinite(b.msd()).all()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base   # everything was given back
+
+    class Failing:
+        alloc_fn = mreg.ALLOC_FN(lambda n, s, c: None)
+        free_fn = mreg.FREE_FN(lambda p, s, c: None)
+    with pytest.raises(mreg.MregError) as e:
+        _reg(mreg, c0, "S1", allocator=Failing())
+    assert e.value.status == mreg.MREG_ERR_OOM
