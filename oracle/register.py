@@ -125,12 +125,21 @@ class Problem:
             return 0.5 * float(np.sum(self.lumped * r * r))
         return 0.5 * float(np.sum(r * r))
 
-    def total_energy(self, u) -> float:
-        """E[u] = D + alpha S (Eq. 1) with S = 1/2 (u_x'K u_x + u_y'K u_y) (S2)."""
-        e = self.data_energy(u)
+    def smoothness(self, u) -> float:
+        """The regulariser S of Eq. 1 for the form at hand: 1/2 (u_x'K u_x +
+        u_y'K u_y) with the P1 stiffness K (S2), or with the graph Laplacian
+        D_m - W of the 1-ring (S0, S1), whose D_m-weighted gradient flow is
+        the diffusion of Eq. 7 with the umbrella operator of Eq. 11-13."""
+        u = np.asarray(u, dtype=np.float64)
         if self.mode == "S2":
-            e += 0.5 * self.alpha * float(np.sum(u * (self.K @ u)))
-        return e
+            L = self.K
+        else:
+            L = sp.diags(self.m) - self.Wadj
+        return 0.5 * float(np.sum(u * (L @ u)))
+
+    def total_energy(self, u) -> float:
+        """E[u] = D + alpha S (Eq. 1)."""
+        return self.data_energy(u) + self.alpha * self.smoothness(u)
 
     def _edge_sample(self, u):
         e = self.edge

@@ -213,3 +213,38 @@ def test_ramp_trajectory_with_repeated_smoothing(small, passes):
     rn = (1 - tau * a @ a) ** n * r0
     np.testing.assert_allclose(u, np.broadcast_to(-(r0 - rn) * a / (a @ a), u.shape), rtol=1e-9,
                                atol=1e-11)
+
+
+@pytest.mark.parametrize("mode", ["S0", "S1", "S2"])
+def test_smoothness_is_a_nonnegative_quadratic_vanishing_on_uniform_fields(small, mode):
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 1.0, mode, "G1")
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        assert pb.smoothness(rng.normal(size=(pb.n, 2))) > 0.0
+    assert abs(pb.smoothness(np.broadcast_to([1.3, -0.4], (pb.n, 2)))) < 1e-9
+    # gradient by central differences equals L u (a symmetric quadratic form)
+    u = rng.normal(size=(pb.n, 2))
+    L = pb.K if mode == "S2" else (np.diag(pb.m) - pb.Wadj.toarray())
+    g = (L @ u) if mode != "S2" else (pb.K @ u)
+    h = 1e-6
+    for a in rng.choice(pb.n, size=5, replace=False):
+        up, um = u.copy(), u.copy()
+        up[a, 0] += h
+        um[a, 0] -= h
+        fd = (pb.smoothness(up) - pb.smoothness(um)) / (2 * h)
+        assert abs(fd - g[a, 0]) <= 1e-6 * max(1.0, abs(g[a, 0]))
+
+
+def test_total_energy_decreases_for_the_umbrella_form(small):
+    """S1 takes an explicit Euclidean step on D and an implicit step on
+    alpha S in the D_m^-1 metric, so it is not an exact gradient flow of
+    D + alpha S; for a small step (tau = 0.1) the total energy still
+    decreases on this pair (with tau = 0.5 it does not)."""
+    pb = register.Problem(small.V, small.T, small.Re, small.Te, 0.1, 0.1, "S1", "G1")
+    u = np.zeros((pb.n, 2))
+    e_prev = pb.total_energy(u)
+    for _ in range(25):
+        u, _ = pb.step(u)
+        e = pb.total_energy(u)
+        assert e < e_prev
+        e_prev = e
