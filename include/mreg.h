@@ -292,9 +292,16 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
  * the value is on the host.                                                 */
 mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream);
 
-/* Data energy (Eq. 4; lumped or edge-midpoint weighted for S2) at the last
- * iterate sampled by mreg_step.  Blocks.                                    */
+/* Energy of Eq. 1 at the current u: E = D + alpha S, FP64.  D is the data
+ * term of the form (Eq. 4: 1/2 sum_i r_i^2 at the nodes for S0 and S1; its
+ * lumped-area weighting for S2 with nodal quadrature; the edge-midpoint
+ * quadrature for the edge form); S = 1/2 (u_x' L u_x + u_y' L u_y) with L the
+ * 1-ring graph Laplacian D_m - W of Eq. 11-13 (S0, S1) or the P1 stiffness
+ * K (S2).  mreg_energy_terms returns D and S separately (either output may
+ * be NULL).  Both block.                                                    */
 mreg_status mreg_energy(mreg_handle* h, double* out_host, void* stream);
+mreg_status mreg_energy_terms(mreg_handle* h, double* data_host, double* smooth_host,
+                              void* stream);
 
 /* Copy u (n_nodes x 2 float, node order of the input mesh) out / in.
  * dst_on_device / src_on_device select device or host memory.  get_u blocks

@@ -913,12 +913,31 @@ mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream) {
   return MREG_OK;
 }
 
-mreg_status mreg_energy(mreg_handle* h, double* out_host, void* stream) {
-  if (!h || !out_host) return fail(MREG_ERR_INVALID_ARG, "handle or output is NULL");
+mreg_status mreg_energy_terms(mreg_handle* h, double* data_host, double* smooth_host,
+                              void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(out_host, h->last, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  // scratch: 2 doubles per block in the warp records (kRec floats per block),
+  // the two results in the spare slots of the stats record
+  const int grid = std::min(h->warp_grid, std::max(1, (h->nV + 255) / 256));
+  const mreg::IterArgs a = h->iter_args(0, 0);
+  CK(mreg::launch_energy_terms(h->form, a, grid, (double*)h->warp_part, h->last + 6, s),
+     "energy kernel launch");
+  double v[2];
+  CK(cudaMemcpyAsync(v, h->last + 6, sizeof v, cudaMemcpyDeviceToHost, s), "copy");
   CK(cudaStreamSynchronize(s), "synchronize");
+  if (data_host) *data_host = v[0];
+  if (smooth_host) *smooth_host = v[1];
+  return MREG_OK;
+}
+
+mreg_status mreg_energy(mreg_handle* h, double* out_host, void* stream) {
+  if (!h || !out_host) return fail(MREG_ERR_INVALID_ARG, "handle or output is NULL");
+  double d = 0.0, sm = 0.0;
+  const mreg_status st = mreg_energy_terms(h, &d, &sm, stream);
+  if (st) return st;
+  *out_host = d + h->alpha * sm;
   return MREG_OK;
 }
 

@@ -39,6 +39,100 @@ __global__ void __launch_bounds__(kIterBlockMax, MINB) k_implicit(const IterArgs
   run_implicit<FORM, GRAD>(a, team, dsm);
 }
 
+// The two terms of Eq. 1 at the current u (a report, not on the iteration
+// path; FP64, fixed summation order): the data term of the form -- 1/2 r^2 at
+// the nodes (S0, S1), weighted by the lumped area (S2 nodal), or at the edge
+// midpoints with their weights (S2 edge form) -- and the regulariser
+// S = 1/2 sum_c u_c' L u_c, L the 1-ring graph Laplacian D_m - W (S0, S1) or
+// the P1 stiffness K (S2), K assembled here from the incident triangles.
+constexpr int kTermsBlock = 256;
+
+__global__ void __launch_bounds__(kTermsBlock) k_energy_terms(const IterArgs a, int form,
+                                                              double* __restrict__ part) {
+  __shared__ double s_d[kTermsBlock], s_s[kTermsBlock];
+  double d = 0.0, sm = 0.0;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < a.nV; i += nth) {
+    const float2 u = a.u[i], Vi = __ldg(a.V + i);
+    if (form != kFormFemEdges) {
+      float gx, gy;
+      const float r = sample_at_node<false>(a, Vi, u, &gx, &gy) - __ldg(a.ReV + i);
+      const double w = form == kFormFemNodes ? (double)__ldg(a.lumped + i) : 1.0;
+      d += 0.5 * w * (double)r * (double)r;
+    }
+    double lx = 0.0, ly = 0.0;   // (L u)_i
+    if (form == kFormFemNodes || form == kFormFemEdges) {
+      for (int k = __ldg(a.inc_ptr + i); k < __ldg(a.inc_ptr + i + 1); ++k) {
+        const int2 jk = __ldg(a.inc_opp + k);
+        const float2 Vj = __ldg(a.V + jk.x), Vk = __ldg(a.V + jk.y);
+        // edges opposite i, j, k of the counter-clockwise triangle (i, j, k)
+        const double eix = (double)Vk.x - Vj.x, eiy = (double)Vk.y - Vj.y;
+        const double ejx = (double)Vi.x - Vk.x, ejy = (double)Vi.y - Vk.y;
+        const double ekx = (double)Vj.x - Vi.x, eky = (double)Vj.y - Vi.y;
+        const double A4 = 2.0 * (ekx * (-ejy) - eky * (-ejx));   // 4 x area
+        const float2 uj = a.u[jk.x], uk = a.u[jk.y];
+        const double kii = (eix * eix + eiy * eiy) / A4, kij = (eix * ejx + eiy * ejy) / A4,
+                     kik = (eix * ekx + eiy * eky) / A4;
+        lx += kii * u.x + kij * uj.x + kik * uk.x;
+        ly += kii * u.y + kij * uj.y + kik * uk.y;
+      }
+    } else {
+      const int b = __ldg(a.adj_ptr + i), e = __ldg(a.adj_ptr + i + 1);
+      lx = (double)(e - b) * u.x;
+      ly = (double)(e - b) * u.y;
+      for (int k = b; k < e; ++k) {
+        const float2 uj = a.u[__ldg(a.adj_col + k)];
+        lx -= uj.x;
+        ly -= uj.y;
+      }
+    }
+    sm += 0.5 * (u.x * lx + u.y * ly);
+  }
+  if (form == kFormFemEdges) {
+    for (int q = tid; q < a.nE; q += nth) {
+      const int2 ab = __ldg(a.edges + q);
+      const float2 va = __ldg(a.V + ab.x), vb = __ldg(a.V + ab.y);
+      const float2 ua = a.u[ab.x], ub = a.u[ab.y];
+      int bx, by;
+      float fx, fy, gx, gy;
+      split_coord(va.x, bx, fx);
+      split_coord(va.y, by, fy);
+      const float ox = fx + 0.5f * ((vb.x - va.x) + (ua.x + ub.x));
+      const float oy = fy + 0.5f * ((vb.y - va.y) + (ua.y + ub.y));
+      const float fq = a.cTe16 ? spline_sample<false>(a.cTe16, a.W, a.H, bx, by, ox, oy, &gx, &gy)
+                               : spline_sample<false>(a.cTe, a.W, a.H, bx, by, ox, oy, &gx, &gy);
+      const double r = (double)fq - __ldg(a.ReQ + q);
+      d += 0.5 * (double)__ldg(a.edge_w + q) * r * r;
+    }
+  }
+  s_d[threadIdx.x] = d;
+  s_s[threadIdx.x] = sm;
+  __syncthreads();
+  for (int w = kTermsBlock / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s_d[threadIdx.x] += s_d[threadIdx.x + w];
+      s_s[threadIdx.x] += s_s[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s_d[0];
+    part[2 * blockIdx.x + 1] = s_s[0];
+  }
+}
+
+__global__ void k_energy_terms_final(const double* __restrict__ part, int nb,
+                                     double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double d = 0.0, sm = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    d += part[2 * b];
+    sm += part[2 * b + 1];
+  }
+  out[0] = d;
+  out[1] = sm;
+}
+
 // Data energy of every iteration of a launch: the sum, in a fixed order, of
 // the warp partials that the sample passes stored (slot it = energy of u^it).
 __global__ void k_energy_final(const float2* __restrict__ epart, int ewarps, int n_iters, int it0,
@@ -76,6 +170,13 @@ void* select_kernel(int form, int grad, int minb) {
 }
 
 }  // namespace
+
+cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* part, double* out,
+                                cudaStream_t s) {
+  k_energy_terms<<<grid, kTermsBlock, 0, s>>>(a, form, part);
+  k_energy_terms_final<<<1, 32, 0, s>>>(part, grid, out);
+  return cudaGetLastError();
+}
 
 cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max_blocks_per_sm) {
   void* k = select_kernel(form, grad, minb);

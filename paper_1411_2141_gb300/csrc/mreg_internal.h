@@ -155,6 +155,11 @@ cudaError_t cluster_prepare(int form, int grad, int C, int chunk, int* max_activ
 cudaError_t launch_cluster(int form, int grad, const IterArgs& a, int C, cudaStream_t s);
 
 // Iteration kernel: occupancy query and cooperative launch.
+// The data term and the regulariser of Eq. 1 at a.u into out[0], out[1]
+// (part: 2 doubles per block of scratch).
+cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* part, double* out,
+                                cudaStream_t s);
+
 // minb: register budget sized for 1 or 2 blocks per SM
 cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max_blocks_per_sm);
 cudaError_t launch_iterate(int form, int grad, int minb, const IterArgs& a, int grid, int block,

@@ -95,7 +95,7 @@ class mreg_stats_t(C.Structure):
 
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
-           "mreg_msd", "mreg_energy", "mreg_get_u", "mreg_set_u", "mreg_get_field",
+           "mreg_msd", "mreg_energy", "mreg_energy_terms", "mreg_get_u", "mreg_set_u", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
            "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
            "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
@@ -133,6 +133,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_warp": ([vp, vp, vp, vp], i32),
         "mreg_msd": ([vp, C.POINTER(dbl), vp], i32),
         "mreg_energy": ([vp, C.POINTER(dbl), vp], i32),
+        "mreg_energy_terms": ([vp, C.POINTER(dbl), C.POINTER(dbl), vp], i32),
         "mreg_get_u": ([vp, vp, i32, vp], i32),
         "mreg_set_u": ([vp, vp, i32, vp], i32),
         "mreg_get_field": ([vp, i32, vp, i32, C.POINTER(i64), vp], i32),
@@ -374,9 +375,17 @@ class Registration:
         return v.value
 
     def energy(self, stream=None) -> float:
+        """E = D + alpha S (Eq. 1) at the current u."""
         v = C.c_double()
         _check(load().mreg_energy(self._h, C.byref(v), _stream_ptr(stream)), "mreg_energy")
         return v.value
+
+    def energy_terms(self, stream=None):
+        """(D, S) at the current u: the data term and the regulariser."""
+        d, sm = C.c_double(), C.c_double()
+        _check(load().mreg_energy_terms(self._h, C.byref(d), C.byref(sm), _stream_ptr(stream)),
+               "mreg_energy_terms")
+        return d.value, sm.value
 
     def get_u(self, out=None, stream=None) -> np.ndarray:
         if out is not None and _is_torch_cuda(out):

@@ -446,3 +446,21 @@ def test_caller_allocator(mreg, c0):
     with pytest.raises(mreg.MregError) as e:
         _reg(mreg, c0, "S1", allocator=Failing())
     assert e.value.status == mreg.MREG_ERR_OOM
+
+
+@pytest.mark.parametrize("mode,grad,quad", [("S0", "G0", "Q0"), ("S1", "G0", "Q0"),
+                                            ("S2", "G1", "Q0"), ("S2", "G1", "Q1")])
+def test_energy_terms_of_eq1(mreg, c0, mode, grad, quad):
+    """mreg_energy = D + alpha S at the current u, against the oracle's data
+    term and regulariser at the GPU's own u (so only the evaluation is
+    compared: D from FP32 spline samples, S in FP64)."""
+    pb = _oracle(c0, mode, grad, quad)
+    with _reg(mreg, c0, mode, grad, quad) as r:
+        r.step(10)
+        u = r.get_u().astype(np.float64)
+        d, sm = r.energy_terms()
+        e = r.energy()
+    d_ref, s_ref = pb.data_energy(u), pb.smoothness(u)
+    assert abs(d - d_ref) <= 1e-5 * d_ref
+    assert abs(sm - s_ref) <= 1e-6 * s_ref + 1e-12
+    assert e == pytest.approx(d + c0.spec.alpha * sm, rel=1e-15)
