@@ -301,6 +301,7 @@ struct mreg_handle {
   int* pcg_it_hist = nullptr;
   double* pcg_res_hist = nullptr;
   float* warp_part = nullptr;
+  float4* aff = nullptr;   // per-triangle affine records of the warp
   double* msd = nullptr;
   int* counters = nullptr;   // [0] uncovered pixels, [1] non-finite values
 
@@ -637,7 +638,8 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_part = take((size_t)2 * h->grid * mreg::kRec * 4), o_bar = take(8),
                o_status = take(4), o_last = take(8 * 8), o_eh = take(kHistCap * 8),
                o_ih = take(kHistCap * 4), o_rh = take(kHistCap * 8),
-               o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_msd = take(8), o_cnt = take(16),
+               o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_aff = take(nT * 32),
+               o_msd = take(8), o_cnt = take(16),
                o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8),
                o_c16 = take(o.coeff_bf16 ? npx * 2 : 0);
   h->mem.alloc = o.alloc;
@@ -687,6 +689,7 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->pcg_it_hist = (int*)(base + o_ih);
   h->pcg_res_hist = (double*)(base + o_rh);
   h->warp_part = (float*)(base + o_wp);
+  h->aff = (float4*)(base + o_aff);
   h->msd = (double*)(base + o_msd);
   h->counters = (int*)(base + o_cnt);
   h->epart = (float2*)(base + o_ep);
@@ -897,6 +900,7 @@ mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* str
   a.Re = h->Re;
   a.out = out_dev;
   a.part = h->warp_part;
+  a.aff = h->aff;
   CK(mreg::launch_warp_msd(a, h->warp_grid, 1.0 / ((double)h->W * h->H), msd_dev,
                            (cudaStream_t)stream),
      "warp kernel launch");

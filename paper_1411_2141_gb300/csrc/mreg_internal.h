@@ -88,6 +88,8 @@ struct WarpArgs {
   const float* Re;       // dense W x H reference pixels
   float* out;            // optional registered image
   float* part;           // one reduction record (kRec floats) per block
+  float4* aff;           // 2 per triangle: the affine form of u over it (scratch
+                         // of the one-pair warp; unused elsewhere)
 };
 
 // Device build of the mesh pre-computation (Algorithm 1): incidence and

@@ -8,11 +8,13 @@
 // formed from the lower-numbered to the higher-numbered node of each edge so
 // that neighbouring triangles classify points on their shared edge alike.
 //
-// Warp: per pixel, barycentric (P1) interpolation of the three node
-// displacements, a 16-tap cubic B-spline sample of Te at x + u(x), and the
-// squared difference with Re, accumulated per thread, reduced per
-// block by warp shuffles in a fixed order, then over blocks in a fixed order;
-// the sums are float-float (hi + lo FP32 pairs), the final mean FP64.
+// Warp: per pixel, the P1 interpolation of the three node displacements
+// (one-pair warp: through a per-triangle affine record formed first; the
+// adjoint and the batched warp: through the barycentric coordinates), a
+// 16-tap cubic B-spline sample of Te at x + u(x), and the squared
+// difference with Re, accumulated per thread, reduced per block by warp
+// shuffles in a fixed order, then over blocks in a fixed order; the sums
+// are float-float (hi + lo FP32 pairs), the final mean FP64.
 #include <climits>
 
 #include "setup_common.cuh"
@@ -43,38 +45,112 @@ __global__ void k_count_equal(const int* __restrict__ p, int64_t n, int v, int* 
 
 constexpr int kWarpBlock = 256;
 
-// The image is walked in 32 x 32 pixel tiles (grid-stride over tiles); in a
-// 256-thread block, thread (x, r) takes the pixels (x, r + 8u), u = 0..3, of
-// its tile.  Neighbouring pixels share spline taps, corners and node
-// displacements, which the 2-D tile keeps in L1, and the four pixels' load
-// chains (owner -> corners -> displacements -> 16 taps) are issued together.
+// The affine form of the P1 interpolant of u over triangle t = (a, b, c):
+// u(x) = u_a + G (x - V_a), with G the (constant) gradient of the linear
+// interpolant, from the barycentric coordinates of x in the undeformed
+// triangle.  Stored as {u_a.x, G_xx, G_xy, V_a.x}, {u_a.y, G_yx, G_yy, V_a.y}:
+// the warp then needs one 32-byte record per pixel instead of the triangle's
+// corners, positions and displacements, and no division.
+__global__ void k_tri_affine(const WarpArgs a) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.nT; t += gridDim.x * blockDim.x) {
+    const int ia = __ldg(a.tri + 3 * t), ib = __ldg(a.tri + 3 * t + 1), ic = __ldg(a.tri + 3 * t + 2);
+    const float2 Va = __ldg(a.V + ia), Vb = __ldg(a.V + ib), Vc = __ldg(a.V + ic);
+    const float2 ua = a.u[ia], ub = a.u[ib], uc = a.u[ic];
+    const float e1x = Vb.x - Va.x, e1y = Vb.y - Va.y, e2x = Vc.x - Va.x, e2y = Vc.y - Va.y;
+    const float inv = 1.0f / (e1x * e2y - e1y * e2x);
+    // x - V_a = l_b e1 + l_c e2, u = u_a + l_b (u_b - u_a) + l_c (u_c - u_a)
+    const float dbx = ub.x - ua.x, dby = ub.y - ua.y, dcx = uc.x - ua.x, dcy = uc.y - ua.y;
+    a.aff[2 * (size_t)t] =
+        make_float4(ua.x, (e2y * dbx - e1y * dcx) * inv, (e1x * dcx - e2x * dbx) * inv, Va.x);
+    a.aff[2 * (size_t)t + 1] =
+        make_float4(ua.y, (e2y * dby - e1y * dcy) * inv, (e1x * dcy - e2x * dby) * inv, Va.y);
+  }
+}
+
+// Warp + MSD over tiles of 32 x 16 pixels (grid-stride over tiles); thread
+// (x, r) of a 256-thread block takes pixels (x, r) and (x, r + 8).  The
+// kernel is bound by load latency, so each stage issues the loads of both
+// pixels before either is consumed and has no data-dependent branch: the
+// owner triangle and Re; the triangle's affine record; the 16 taps of the
+// 4 x 4 coefficient window (its index clamped into the image, so the loads
+// are always in bounds).  A pixel whose window is not inside the image
+// (the mirror extension applies) or whose owner is missing is settled
+// afterwards, on the per-tap path with the mirror fold.
 // OUT: also write R (a separate instance, so that the MSD-only loop has no
 // stores for the compiler to order loads against).
 constexpr int kWarpTile = 32;
+constexpr int kWarpNP = 2;                // pixels per thread
+constexpr int kWarpTileH = 8 * kWarpNP;   // tile height
+constexpr int kWarpMinBlocks = 4;         // register budget: 4 blocks per SM
 static_assert(kWarpBlock == kWarpTile * 8, "one tile row per 32 threads, 8 rows per pass");
 
-template <bool OUT>
-__global__ void __launch_bounds__(kWarpBlock) k_warp_msd(const WarpArgs a) {
+template <bool OUT, class C>
+__global__ void __launch_bounds__(kWarpBlock, kWarpMinBlocks) k_warp_msd(const WarpArgs a,
+                                                                         const C* __restrict__ coef) {
   __shared__ float s_red[kMaxWarps * kRec];
   const int W = a.W, H = a.H;
-  const int tx = (W + kWarpTile - 1) / kWarpTile, ty = (H + kWarpTile - 1) / kWarpTile;
+  const int tx = (W + kWarpTile - 1) / kWarpTile, ty = (H + kWarpTileH - 1) / kWarpTileH;
   const int ntiles = tx * ty;
+  const bool small = W < 4 || H < 4;   // no 4 x 4 window inside the image
   ff acc = ff_zero();
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x = (tile % tx) * kWarpTile + (threadIdx.x & 31);
-    const int y0 = (tile / tx) * kWarpTile + (threadIdx.x >> 5);
-    float R[4], d[4];
-    bool ok[4];
+    const int y0 = (tile / tx) * kWarpTileH + (threadIdx.x >> 5);
+    int64_t p[kWarpNP];
+    int t[kWarpNP];
+    float re[kWarpNP];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int y = y0 + 8 * u;
-      ok[u] = x < W && y < H && warp_pixel(a, (int64_t)y * W + x, R[u], d[u]);
+    for (int k = 0; k < kWarpNP; ++k) {
+      const bool in = x < W && y0 + 8 * k < H;
+      p[k] = in ? (int64_t)(y0 + 8 * k) * W + x : 0;
+      t[k] = __ldg(a.pix_tri + p[k]);
+      re[k] = __ldg(a.Re + p[k]);
+      t[k] = (in && (unsigned)t[k] < (unsigned)a.nT) ? t[k] : -1;
+    }
+    float ux[kWarpNP], uy[kWarpNP];
+#pragma unroll
+    for (int k = 0; k < kWarpNP; ++k) {
+      const size_t ts = t[k] < 0 ? 0 : (size_t)t[k];
+      const float4 fx = a.aff[2 * ts], fy = a.aff[2 * ts + 1];
+      const float dx = (float)x - fx.w, dy = (float)(y0 + 8 * k) - fy.w;
+      ux[k] = fx.x + fx.y * dx + fx.z * dy;
+      uy[k] = fy.x + fy.y * dx + fy.z * dy;
+    }
+    float R[kWarpNP];
+    bool edge[kWarpNP];
+#pragma unroll
+    for (int k = 0; k < kWarpNP; ++k) {
+      // the interior case of spline_sample, with the same position split
+      const float ox = fminf(fmaxf(ux[k], -1.0e7f), 1.0e7f);
+      const float oy = fminf(fmaxf(uy[k], -1.0e7f), 1.0e7f);
+      const float fx = floorf(ox), fy = floorf(oy);
+      const int ix = x + (int)fx, iy = y0 + 8 * k + (int)fy;
+      float wx[4], wy[4];
+      cubic_weights(ox - fx, wx);
+      cubic_weights(oy - fy, wy);
+      edge[k] = small || !(ix >= 1 && ix + 2 < W && iy >= 1 && iy + 2 < H);
+      R[k] = 0.0f;
+      if (!small) {
+        const int cx = min(max(ix - 1, 0), W - 4), cy = min(max(iy - 1, 0), H - 4);
+        const C* c = coef + (int64_t)cy * W + cx;
+        float v = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const C* row = c + (int64_t)m * W;
+          const float c0 = load_coef(row), c1 = load_coef(row + 1);
+          const float c2 = load_coef(row + 2), c3 = load_coef(row + 3);
+          v += wy[m] * (wx[0] * c0 + wx[1] * c1 + wx[2] * c2 + wx[3] * c3);
+        }
+        R[k] = v;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (!ok[u]) continue;
-      if (OUT) a.out[(int64_t)(y0 + 8 * u) * W + x] = R[u];
-      acc = ff_add(acc, ff_prod(d[u], d[u]));
+    for (int k = 0; k < kWarpNP; ++k) {
+      if (t[k] < 0) continue;
+      if (edge[k]) R[k] = spline_sample<false>(coef, W, H, x, y0 + 8 * k, ux[k], uy[k], nullptr, nullptr);
+      if (OUT) a.out[p[k]] = R[k];
+      const float d = R[k] - re[k];
+      acc = ff_add(acc, ff_prod(d, d));
     }
   }
   float none[1] = {0.0f};
@@ -256,9 +332,15 @@ cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tp
 }
 
 int warp_grid_blocks(int W, int H, int num_sms) {
-  const int64_t need = (int64_t)((W + kWarpTile - 1) / kWarpTile) * ((H + kWarpTile - 1) / kWarpTile);
-  const int64_t cap = (int64_t)num_sms * 8;
-  return (int)(need < cap ? need : cap);
+  const int64_t need =
+      (int64_t)((W + kWarpTile - 1) / kWarpTile) * ((H + kWarpTileH - 1) / kWarpTileH);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_msd<false, float>, kWarpBlock,
+                                                    0) != cudaSuccess || per_sm < 1)
+    per_sm = kWarpMinBlocks;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  const int64_t g = need < cap ? need : cap;
+  return (int)(g > 0 ? g : 1);
 }
 
 cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int H, int* pix_tri,
@@ -274,8 +356,17 @@ cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int
 
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
                             cudaStream_t s) {
-  if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a);
-  else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a);
+  if (a.nT > 0) {
+    const int gt = (a.nT + 255) / 256 < 8192 ? (a.nT + 255) / 256 : 8192;
+    k_tri_affine<<<gt, 256, 0, s>>>(a);
+  }
+  if (a.cTe16) {
+    if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a, a.cTe16);
+    else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a, a.cTe16);
+  } else {
+    if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a, a.cTe);
+    else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a, a.cTe);
+  }
   if (msd_out) k_msd_final<<<1, 32, 0, s>>>(a.part, grid, inv_count, msd_out);
   return cudaGetLastError();
 }
