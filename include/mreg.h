@@ -131,8 +131,8 @@ typedef struct {
   double pcg_rtol;     /* stop when ||b - A u'||_2 <= rtol ||b||_2, residual
                           formed in FP64, per component     (default 1e-7)  */
   int32_t block_size;  /* threads per block of the iteration kernel (multiple of
-                          32, <= 512); 0 = 256, or 512 when the mesh has more
-                          nodes than 256 per SM                             */
+                          32, <= 512); 0 = 512 with two lanes per node or when
+                          the mesh has more nodes than 256 per SM, else 256 */
   int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
   int32_t engine;      /* MREG_ENGINE_*                     (default AUTO)  */
   int32_t coeff_bf16;  /* 1: the iteration and the warp read Te's B-spline
@@ -162,6 +162,14 @@ typedef struct {
                           sized for: 1 (up to 128 registers per thread) or 2
                           (up to 64, the rest in local memory); 0 = 1 (the
                           batched engine's autotuner tries both).           */
+  int32_t node_lanes;  /* grid engine, S1/S2: lanes of a warp per node.  2:
+                          the two lanes split the node's neighbour and
+                          incident-triangle lists and add their parts by a
+                          shuffle (needs team_blocks_per_sm 1); 1: one lane
+                          per node; 0 = automatic: 2 when one node per lane
+                          pair fits the grid (at most 256 nodes per SM, the
+                          block then 512 threads), else 1.  Other modes and
+                          engines accept 0 or 1.                            */
   /* Device memory.  With alloc non-NULL every device buffer of the handle or
    * batch comes from alloc(bytes, stream, alloc_ctx) -- stream being the
    * stream of the call that allocates -- and goes back through
@@ -189,6 +197,7 @@ typedef struct {
   int32_t block_size;
   int32_t device_status;       /* raw device status bits (0 = clean)         */
   int32_t engine;              /* MREG_ENGINE_GRID or MREG_ENGINE_CLUSTER     */
+  int32_t node_lanes;          /* lanes per node of the iteration kernel      */
 } mreg_stats_t;
 
 /* Fields readable with mreg_get_field (mainly for parity tests). */

@@ -266,6 +266,7 @@ struct mreg_handle {
   int form = 0, grad = 0;
   int grid = 0, block = 0, warp_grid = 0;
   int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
+  int lanes = 1;  // lanes per node of the iteration kernel
   int engine = MREG_ENGINE_GRID, cl_size = 0, cl_chunk = 0;
   float area_floor = 0.0f;
   int iterations_done = 0, last_n_iters = 0, last_force_buf = 0;
@@ -414,6 +415,12 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
     return fail(MREG_ERR_INVALID_ARG, "smooth_passes must be in [0, 64]");
   if (o.smooth_passes > 1 && o.mode != MREG_MODE_EXPLICIT)
     return fail(MREG_ERR_INVALID_ARG, "smooth_passes > 1 needs the explicit mode");
+  if (o.node_lanes < 0 || o.node_lanes > 2)
+    return fail(MREG_ERR_INVALID_ARG, "node_lanes must be 0, 1 or 2");
+  if (o.node_lanes == 2 && (o.mode == MREG_MODE_EXPLICIT || o.team_blocks_per_sm == 2 ||
+                            o.engine == MREG_ENGINE_CLUSTER))
+    return fail(MREG_ERR_INVALID_ARG,
+                "node_lanes 2 needs an implicit mode on the grid engine with team_blocks_per_sm 1");
   const double l = o.lambda < 0.0 ? tau * alpha : o.lambda;
   if (!std::isfinite(l)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
   *lam = l;
@@ -567,14 +574,20 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   // 250k-node pair (114 against 140 with 256: fewer blocks make the grid
   // barrier cheaper).  The 64-register variant (team_blocks_per_sm = 2) was
   // slower on both (its spills and the larger grid), so it is opt-in.
-  h->block = o.block_size ? o.block_size
-                          : ((int64_t)(h->nV + 255) / 256 > h->num_sms ? 512 : 256);
+  // Two lanes per node (the neighbour lists split between them) when one
+  // node per lane pair fits the grid: the node work of a phase is a chain of
+  // dependent loads and float-float arithmetic per lane, with few warps per
+  // SM to hide it, so halving each lane's chain shortens the phase.
   h->minb = o.team_blocks_per_sm ? o.team_blocks_per_sm : 1;
+  const bool small_mesh = (int64_t)(h->nV + 255) / 256 <= h->num_sms;
+  h->lanes = o.node_lanes ? o.node_lanes
+                          : (o.mode != MREG_MODE_EXPLICIT && h->minb == 1 && small_mesh ? 2 : 1);
+  h->block = o.block_size ? o.block_size : (h->lanes == 2 || !small_mesh ? 512 : 256);
   int per_sm = 0;
-  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, h->minb, &per_sm), "occupancy");
+  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, h->minb, h->lanes, &per_sm), "occupancy");
   if (per_sm < 1) return fail(MREG_ERR_INVALID_ARG, "block_size %d does not fit on an SM", h->block);
   const int max_grid = per_sm * h->num_sms;
-  const int want = (h->nV + h->block - 1) / h->block;
+  const int want = (int)(((int64_t)h->nV * h->lanes + h->block - 1) / h->block);
   h->grid = o.grid_blocks ? o.grid_blocks : std::max(1, std::min(want, max_grid));
   if (h->grid > max_grid)
     return fail(MREG_ERR_INVALID_ARG, "grid_blocks %d exceeds the %d co-resident blocks", h->grid,
@@ -782,7 +795,8 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
       CK(mreg::launch_cluster(h->form, h->grad, a, h->cl_size, (cudaStream_t)stream),
          "cluster iteration kernel launch");
     } else {
-      CK(mreg::launch_iterate(h->form, h->grad, h->minb, a, h->grid, h->block, (cudaStream_t)stream),
+      CK(mreg::launch_iterate(h->form, h->grad, h->minb, h->lanes, a, h->grid, h->block,
+                              (cudaStream_t)stream),
          "iteration kernel launch");
     }
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
@@ -1024,6 +1038,7 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
     out->block_size = h->engine == MREG_ENGINE_CLUSTER ? mreg::cluster_block_size() : h->block;
     out->device_status = status;
     out->engine = h->engine;
+    out->node_lanes = h->engine == MREG_ENGINE_CLUSTER ? 1 : h->lanes;
   }
   if (status & mreg::kStatusBarrierTimeout)
     return fail(MREG_ERR_DEVICE_CHECK, "a grid barrier of the iteration kernel timed out");

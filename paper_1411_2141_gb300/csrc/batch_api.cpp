@@ -250,6 +250,8 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   if (o.team_ctas != 0 && o.team_ctas != 1 && o.team_ctas != 2 && o.team_ctas != 4 &&
       o.team_ctas != 8 && o.team_ctas != 16)
     return fail(MREG_ERR_INVALID_ARG, "team_ctas must be 0, 1, 2, 4, 8 or 16");
+  if (o.node_lanes > 1)
+    return fail(MREG_ERR_INVALID_ARG, "the batched engine runs one lane per node (node_lanes 0 or 1)");
 
   // host topology of every pair, built on worker threads (pairs are
   // independent); the first failing pair (lowest index) is reported
@@ -759,6 +761,7 @@ mreg_status mreg_batch_stats(mreg_batch* b, int32_t pair, mreg_stats_t* out, voi
     out->block_size = b->block;
     out->device_status = status;
     out->engine = 0;   // the batched engine has no one-pair engine id
+    out->node_lanes = 1;
   }
   if (status & mreg::kStatusNotConverged)
     return fail(MREG_ERR_NOT_CONVERGED, "pair %d: %d solves stopped at the cap of %d CG iterations",

@@ -30,13 +30,14 @@ __global__ void __launch_bounds__(kIterBlockMax, MINB) k_explicit(const IterArgs
   run_explicit<GRAD>(a, team, dsm);
 }
 
-template <int FORM, int GRAD, int MINB>
+// L: lanes per node (1, or 2 with the neighbour lists split between them).
+template <int FORM, int GRAD, int MINB, int L>
 __global__ void __launch_bounds__(kIterBlockMax, MINB) k_implicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
   GridTeam team{GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull}, &s_flag,
                 (int)blockIdx.x, (int)gridDim.x};
-  run_implicit<FORM, GRAD>(a, team, dsm);
+  run_implicit<FORM, GRAD, L>(a, team, dsm);
 }
 
 // The two terms of Eq. 1 at the current u (a report, not on the iteration
@@ -151,22 +152,24 @@ __global__ void k_energy_final(const float2* __restrict__ epart, int ewarps, int
   }
 }
 
-template <int MINB>
+template <int MINB, int L>
 void* select_kernel_m(int form, int grad) {
   switch (form * 2 + (grad ? 1 : 0)) {
-    case 0: return (void*)k_explicit<0, MINB>;
-    case 1: return (void*)k_explicit<1, MINB>;
-    case 2: return (void*)k_implicit<kFormUmbrella, 0, MINB>;
-    case 3: return (void*)k_implicit<kFormUmbrella, 1, MINB>;
-    case 4: return (void*)k_implicit<kFormFemNodes, 0, MINB>;
-    case 5: return (void*)k_implicit<kFormFemNodes, 1, MINB>;
-    case 7: return (void*)k_implicit<kFormFemEdges, 1, MINB>;
+    case 0: return L == 1 ? (void*)k_explicit<0, MINB> : nullptr;
+    case 1: return L == 1 ? (void*)k_explicit<1, MINB> : nullptr;
+    case 2: return (void*)k_implicit<kFormUmbrella, 0, MINB, L>;
+    case 3: return (void*)k_implicit<kFormUmbrella, 1, MINB, L>;
+    case 4: return (void*)k_implicit<kFormFemNodes, 0, MINB, L>;
+    case 5: return (void*)k_implicit<kFormFemNodes, 1, MINB, L>;
+    case 7: return (void*)k_implicit<kFormFemEdges, 1, MINB, L>;
     default: return nullptr;
   }
 }
 
-void* select_kernel(int form, int grad, int minb) {
-  return minb == 2 ? select_kernel_m<2>(form, grad) : select_kernel_m<1>(form, grad);
+// Two lanes per node only with the full register budget (one block per SM).
+void* select_kernel(int form, int grad, int minb, int lanes) {
+  if (lanes == 2) return minb == 1 ? select_kernel_m<1, 2>(form, grad) : nullptr;
+  return minb == 2 ? select_kernel_m<2, 1>(form, grad) : select_kernel_m<1, 1>(form, grad);
 }
 
 }  // namespace
@@ -178,8 +181,9 @@ cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* p
   return cudaGetLastError();
 }
 
-cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max_blocks_per_sm) {
-  void* k = select_kernel(form, grad, minb);
+cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes,
+                               int* max_blocks_per_sm) {
+  void* k = select_kernel(form, grad, minb, lanes);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -187,9 +191,9 @@ cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k, block, smem);
 }
 
-cudaError_t launch_iterate(int form, int grad, int minb, const IterArgs& a, int grid, int block,
-                           cudaStream_t s) {
-  void* k = select_kernel(form, grad, minb);
+cudaError_t launch_iterate(int form, int grad, int minb, int lanes, const IterArgs& a, int grid,
+                           int block, cudaStream_t s) {
+  void* k = select_kernel(form, grad, minb, lanes);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

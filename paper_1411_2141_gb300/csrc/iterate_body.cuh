@@ -129,16 +129,56 @@ struct Topo {
   }
 };
 
+// A node is handled by L adjacent lanes of a warp (L = 1 or 2).  With L = 2
+// each lane takes every other group of the node's neighbour (incidence)
+// list, and the two parts are added by a shuffle within the pair; IEEE and
+// float-float additions are commutative, so both lanes obtain the same
+// total, and only the first lane (lead) stores and reduces.  The two lanes
+// of a node always run the same node loop together (their node index is
+// the same), so the pair mask is exact.
+template <int L>
+struct NodeLanes {
+  int sub;         // part of this lane: 0 .. L-1
+  unsigned mask;   // the lanes of this node
+  __device__ __forceinline__ static NodeLanes make() {
+    NodeLanes n;
+    n.sub = L == 1 ? 0 : (int)(threadIdx.x & (L - 1));
+    n.mask = L == 1 ? 0xffffffffu : (3u << ((threadIdx.x & 31) & ~1u));
+    return n;
+  }
+  __device__ __forceinline__ bool lead() const { return sub == 0; }
+  __device__ __forceinline__ float sum(float v) const {
+    if (L == 1) return v;
+    return v + __shfl_xor_sync(mask, v, 1);
+  }
+  __device__ __forceinline__ ff sum(ff v) const {
+    if (L == 1) return v;
+    return ff_add(v, ff{__shfl_xor_sync(mask, v.hi, 1), __shfl_xor_sync(mask, v.lo, 1)});
+  }
+  template <int FORM>
+  __device__ __forceinline__ void sum(AxAcc<FORM>& A) const {
+    if (FORM == kFormUmbrella) {
+      A.sx = sum(A.sx);
+      A.sy = sum(A.sy);
+    } else {
+      A.ax = sum(A.ax);
+      A.ay = sum(A.ay);
+    }
+  }
+};
+static_assert(kIterBlockMax % 2 == 0, "a node's lanes share a warp");
+
 // Eq. 10 with Eq. 9 (see mesh_gradient in iterate_common.cuh), gathering the
 // incident triangles two at a time.
-template <class DISP, class FVAL>
+template <int L, class DISP, class FVAL>
 __device__ __forceinline__ float2 mesh_gradient_c(const IterArgs& a, const Topo& T, bool cached,
                                                   const DISP& disp, const FVAL& fval, int i,
-                                                  float2 Vi, float2 ui, float fi) {
+                                                  float2 Vi, float2 ui, float fi,
+                                                  const NodeLanes<L>& nl) {
   float nx = 0.0f, ny = 0.0f, den = 0.0f;
   int beg, deg;
   T.irow(a, cached, i, beg, deg);
-  for (int k0 = 0; k0 < deg; k0 += 2) {
+  for (int k0 = 2 * nl.sub; k0 < deg; k0 += 2 * L) {
     int2 jk[2];
     float2 Vj[2], Vk[2], uj[2], uk[2];
     float fj[2], fk[2];
@@ -168,17 +208,20 @@ __device__ __forceinline__ float2 mesh_gradient_c(const IterArgs& a, const Topo&
       den += area;
     }
   }
+  nx = nl.sum(nx);
+  ny = nl.sum(ny);
+  den = nl.sum(den);
   if (den > 0.0f) return make_float2(nx / den, ny / den);
   return make_float2(0.0f, 0.0f);
 }
 
-template <int FORM, class DISP, class FVAL>
+template <int FORM, int L, class DISP, class FVAL>
 __device__ __forceinline__ float2 neighbour_force_c(const IterArgs& a, const Topo& T, bool cached,
                                                     const DISP& disp, const FVAL& fval, int i,
-                                                    float2 ui, float fi) {
+                                                    float2 ui, float fi, const NodeLanes<L>& nl) {
   if (FORM == kFormFemEdges) return neighbour_force<FORM>(a, disp, fval, i, ui, fi);
   const float2 Vi = __ldg(a.V + i);
-  const float2 g = mesh_gradient_c(a, T, cached, disp, fval, i, Vi, ui, fi);
+  const float2 g = mesh_gradient_c<L>(a, T, cached, disp, fval, i, Vi, ui, fi, nl);
   const float r = fi - __ldg(a.ReV + i);
   const float wr = (FORM == kFormFemNodes) ? __ldg(a.lumped + i) * r : r;
   return make_float2(wr * g.x, wr * g.y);
@@ -190,9 +233,10 @@ __device__ __forceinline__ float2 neighbour_force_c(const IterArgs& a, const Top
   do {                              \
     if (!team.sync()) return false; \
   } while (0)
-// node loop: thread-strided; the first node of each thread has cached topology
+// node loop: strided over the node slots (ntid = tid / L of nnth = nth / L);
+// the first node of each slot has cached topology
 #define FOR_NODES(i, cached) \
-  for (int i = tid, slot_ = 0; i < nV; i += nth, ++slot_) if (const bool cached = slot_ == 0; true)
+  for (int i = ntid, slot_ = 0; i < nV; i += nnth, ++slot_) if (const bool cached = slot_ == 0; true)
 
 // One Eq. 14 pass at node i: (1 - l) v_i + l mean_{j in N1(i)} v_j.
 __device__ __forceinline__ float2 smooth_node(const IterArgs& a, const Topo& T, bool cached,
@@ -228,9 +272,11 @@ __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsi
   const int nV = a.nV;
   const int bd = blockDim.x;
   const int gwarp = tid >> 5;   // energy partials are kept per warp
+  const int ntid = tid, nnth = nth;   // one lane per node
   Topo T{(int*)dsm, (float*)(dsm + (size_t)kCacheA * bd * sizeof(int)),
          (int2*)(dsm + (size_t)kCacheA * bd * (sizeof(int) + sizeof(float))), bd, (int)threadIdx.x};
   if (tid < nV) T.fill(a, tid);
+  const NodeLanes<1> nl = NodeLanes<1>::make();
   const DispPlain disp{a.u};
   const FPlain fval{a.f};
 
@@ -256,7 +302,7 @@ __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsi
     if (GRAD == 0) {   // force (Eq. 6, 9, 10) and the step (Eq. 5)
       FOR_NODES(i, cached) {
         const float2 ui = a.u[i];
-        const float2 Fi = neighbour_force_c<kFormExplicit>(a, T, cached, disp, fval, i, ui, a.f[i]);
+        const float2 Fi = neighbour_force_c<kFormExplicit, 1>(a, T, cached, disp, fval, i, ui, a.f[i], nl);
         F[i] = Fi;
         u0[i] = make_float2(ui.x - a.tau * Fi.x, ui.y - a.tau * Fi.y);
       }
@@ -293,25 +339,28 @@ __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsi
 // Solve set-up for node i: b, r0 = b - A x0 (float-float) and z0 = D^-1 r0
 // into the CG state (x is rewritten with its own value); adds ||b||^2,
 // ||r0||^2 and r0.z0 (x, y) to acc[0..6).
-template <int FORM>
+template <int FORM, int L>
 __device__ __forceinline__ void init_node_c(const IterArgs& a, const Topo& T, bool cached,
                                             const DispCg& disp, float4* st, int i, float2 xi,
-                                            float2 Fi, float* acc) {
+                                            float2 Fi, float* acc, const NodeLanes<L>& nl) {
   int beg, deg;
-      T.arow(a, cached, i, beg, deg);
+  T.arow(a, cached, i, beg, deg);
   const ff tau = ff_load(a.tau_ff);
   ff bx, by;
   AxAcc<FORM> A;
-  A.init(a, i, xi);
+  A.init_part(a, i, xi, nl.lead());
   if (FORM == kFormUmbrella) {
     bx = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.x)), xi.x), (float)deg);   // D_m (u - tau F)
     by = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.y)), xi.y), (float)deg);
-  } else {
+  } else if (nl.lead()) {
     const float md = __ldg(a.Mdiag + i);   // M u - tau F
     bx = ff_prod(md, xi.x);
     by = ff_prod(md, xi.y);
+  } else {
+    bx = ff_zero();
+    by = ff_zero();
   }
-  for (int k0 = 0; k0 < deg; k0 += 4) {
+  for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
     float2 xj[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) xj[u] = (k0 + u < deg) ? disp(T.adj(a, cached, beg, k0 + u)) : make_float2(0.0f, 0.0f);
@@ -326,11 +375,15 @@ __device__ __forceinline__ void init_node_c(const IterArgs& a, const Topo& T, bo
       }
     }
   }
+  nl.sum(A);
   if (FORM != kFormUmbrella) {
+    bx = nl.sum(bx);
+    by = nl.sum(by);
     bx = ff_add(bx, ff_neg(ff_mul_f(tau, Fi.x)));
     by = ff_add(by, ff_neg(ff_mul_f(tau, Fi.y)));
   }
   A.finish(a, deg, xi);
+  if (!nl.lead()) return;
   a.b[i] = make_float4(bx.hi, bx.lo, by.hi, by.lo);
   const float2 r = make_float2(ff_to_f(ff_add(bx, ff_neg(A.ax))), ff_to_f(ff_add(by, ff_neg(A.ay))));
   const float di = __ldg(a.dinv + i);
@@ -350,20 +403,21 @@ __device__ __forceinline__ void init_node_c(const IterArgs& a, const Topo& T, bo
 // One CG step for node i (state st -> st_out).  VERIFY: also the true
 // residual of x' (float-float, into a.rt and c[4..6)) and the sample at x'.
 // Adds gamma' = r'.z' (x, y), delta' = w'.z' and ||r'||^2 to c[0..4), c[6..8).
-template <int FORM, int GRAD, bool VERIFY>
+template <int FORM, int GRAD, bool VERIFY, int L>
 __device__ __forceinline__ void cg_step_node(const IterArgs& a, const Topo& T, bool cached,
                                              const float4* st, float4* st_out, int i,
-                                             const CgStep& step, float* c, ff& e, float2* Fn) {
+                                             const CgStep& step, float* c, ff& e, float2* Fn,
+                                             const NodeLanes<L>& nl) {
   int beg, deg;
-      T.arow(a, cached, i, beg, deg);
+  T.arow(a, cached, i, beg, deg);
   const Cg ci = load_cg(st, i);
   const CgNext ni = cg_next(ci, __ldg(a.dinv + i), step);
   const float ad = a_diag<FORM>(a, i, deg);
-  float wx = ad * ni.z.x, wy = ad * ni.z.y;
+  float wx = nl.lead() ? ad * ni.z.x : 0.0f, wy = nl.lead() ? ad * ni.z.y : 0.0f;
   AxAcc<FORM> A;
-  if (VERIFY) A.init(a, i, ni.x);
+  if (VERIFY) A.init_part(a, i, ni.x, nl.lead());
   constexpr int G = VERIFY ? 2 : 4;   // neighbours gathered together
-  for (int k0 = 0; k0 < deg; k0 += G) {
+  for (int k0 = G * nl.sub; k0 < deg; k0 += G * L) {
     int jj[G];
     float dd[G];
     float4 s1[G], s2[G], s0[G];
@@ -394,6 +448,10 @@ __device__ __forceinline__ void cg_step_node(const IterArgs& a, const Topo& T, b
       }
     }
   }
+  wx = nl.sum(wx);
+  wy = nl.sum(wy);
+  if (VERIFY) nl.sum(A);
+  if (!nl.lead()) return;
   Cg out;
   out.x = ni.x;
   out.z = ni.z;
@@ -423,7 +481,7 @@ __device__ __forceinline__ void cg_step_node(const IterArgs& a, const Topo& T, b
   }
 }
 
-template <int FORM, int GRAD, class TEAM>
+template <int FORM, int GRAD, int L = 1, class TEAM>
 __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsigned char* dsm) {
   __shared__ float s_red[kMaxWarps * kRec];
   __shared__ float s_tot[2 * kRec];   // alternates with par
@@ -437,9 +495,11 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
   constexpr bool kEdges = FORM == kFormFemEdges;
   // the spline-gradient node forms get F from the sample itself
   constexpr bool kForceInSample = GRAD == 1 && !kEdges;
+  const int ntid = tid / L, nnth = nth / L;   // node slots
+  const NodeLanes<L> nl = NodeLanes<L>::make();
   Topo T{(int*)dsm, (float*)(dsm + (size_t)kCacheA * bd * sizeof(int)),
          (int2*)(dsm + (size_t)kCacheA * bd * (sizeof(int) + sizeof(float))), bd, (int)threadIdx.x};
-  if (tid < nV) T.fill(a, tid);
+  if (ntid < nV) T.fill(a, ntid);
   float4* const cg[2] = {a.cg, a.cg + (size_t)3 * nV};
   int par = 0;   // half of the partial-sum buffer used by the next reduction
 
@@ -471,9 +531,12 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
       } else {
         FOR_NODES(i, cached) {
           const float2 xi = disp(i);
-          float2 Fi;
-          e = ff_add_f(e, sample_node<FORM, GRAD>(a, i, xi, a.f + i, F + i, &Fi));
-          if (kForceInSample) init_node_c<FORM>(a, T, cached, disp, cg[q], i, xi, Fi, init);
+          float2 Fi, Fd;
+          float fd;
+          const float ei = sample_node<FORM, GRAD>(a, i, xi, nl.lead() ? a.f + i : &fd,
+                                                   nl.lead() ? F + i : &Fd, &Fi);
+          if (nl.lead()) e = ff_add_f(e, ei);
+          if (kForceInSample) init_node_c<FORM, L>(a, T, cached, disp, cg[q], i, xi, Fi, init, nl);
         }
       }
       warp_energy_store(e, a.epart + (size_t)it * a.ewarps, gwarp);
@@ -495,10 +558,10 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
         if (kForceInSample) {
           Fi = F[i];   // formed with the sample
         } else {
-          Fi = neighbour_force_c<FORM>(a, T, cached, disp, fval, i, xi, a.f[i]);
-          F[i] = Fi;
+          Fi = neighbour_force_c<FORM, L>(a, T, cached, disp, fval, i, xi, a.f[i], nl);
+          if (nl.lead()) F[i] = Fi;
         }
-        init_node_c<FORM>(a, T, cached, disp, cg[q], i, xi, Fi, acc);
+        init_node_c<FORM, L>(a, T, cached, disp, cg[q], i, xi, Fi, acc, nl);
       }
       block_record<6, false>(acc, ff_zero(), MY_REC, s_red);
       SYNC_OR_LEAVE();
@@ -532,11 +595,11 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
         float c2[2] = {0.0f, 0.0f};
         FOR_NODES(i, cached) {
           int beg, deg;
-      T.arow(a, cached, i, beg, deg);
+          T.arow(a, cached, i, beg, deg);
           const float4 xz = cg[q][3 * (size_t)i];
           const float ad = a_diag<FORM>(a, i, deg);
-          float wx = ad * xz.z, wy = ad * xz.w;
-          for (int k0 = 0; k0 < deg; k0 += 4) {
+          float wx = nl.lead() ? ad * xz.z : 0.0f, wy = nl.lead() ? ad * xz.w : 0.0f;
+          for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
             float4 v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -549,6 +612,9 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
               wy = __fmaf_rn(ao, v[u].w, wy);
             }
           }
+          wx = nl.sum(wx);
+          wy = nl.sum(wy);
+          if (!nl.lead()) continue;
           cg[q][3 * (size_t)i + 2] = make_float4(wx, wy, 0.0f, 0.0f);
           c2[0] += wx * xz.z;
           c2[1] += wy * xz.w;
@@ -572,7 +638,7 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
       float c8[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
       ff e = ff_zero();
       if (verify) {
-        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, true>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn);
+        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, true, L>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn, nl);
         if (kEdges) {
           for (int q2 = tid; q2 < a.nE; q2 += nth) {
             const int2 ab = __ldg(a.edges + q2);
@@ -584,7 +650,7 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
         warp_energy_store(e, a.epart + (size_t)(it + 1) * a.ewarps, gwarp);
         block_record<8, false>(c8, ff_zero(), MY_REC, s_red);
       } else {
-        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, false>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn);
+        FOR_NODES(i, cached) cg_step_node<FORM, GRAD, false, L>(a, T, cached, cg[q], cg[q ^ 1], i, step, c8, e, Fn, nl);
         block_record<8, false>(c8, e, MY_REC, s_red);
       }
       SYNC_OR_LEAVE();
@@ -643,8 +709,8 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
             xz.w = __fmul_rn(di, rt.y);
           }
           const float ad = a_diag<FORM>(a, i, deg);
-          float wx = ad * xz.z, wy = ad * xz.w;
-          for (int k0 = 0; k0 < deg; k0 += 4) {
+          float wx = nl.lead() ? ad * xz.z : 0.0f, wy = nl.lead() ? ad * xz.w : 0.0f;
+          for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
             int jj[4];
             float dd[4];
             float2 rj[4];
@@ -670,6 +736,9 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
               wy = __fmaf_rn(ao, zy, wy);
             }
           }
+          wx = nl.sum(wx);
+          wy = nl.sum(wy);
+          if (!nl.lead()) continue;
           node[0] = xz;   // a converged component keeps its bits
           node[1] = pr;
           node[2] = make_float4(wx, wy, 0.0f, 0.0f);

@@ -233,6 +233,16 @@ struct AxAcc {
       ay = ff_prod(ad, xi.y);
     }
   }
+  // the partial sums of a lane that is not its node's first start from zero
+  // (the diagonal term is the first lane's)
+  __device__ __forceinline__ void init_part(const IterArgs& a, int i, float2 xi, bool lead) {
+    if (FORM == kFormUmbrella || lead) {
+      init(a, i, xi);
+    } else {
+      ax = ff_zero();
+      ay = ff_zero();
+    }
+  }
   __device__ __forceinline__ void add(const IterArgs& a, int k, float2 xj) {
     if (FORM == kFormUmbrella) {
       sx = ff_add_f(sx, xj.x);

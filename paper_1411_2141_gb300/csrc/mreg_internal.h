@@ -162,10 +162,12 @@ cudaError_t launch_cluster(int form, int grad, const IterArgs& a, int C, cudaStr
 cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* part, double* out,
                                 cudaStream_t s);
 
-// minb: register budget sized for 1 or 2 blocks per SM
-cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int* max_blocks_per_sm);
-cudaError_t launch_iterate(int form, int grad, int minb, const IterArgs& a, int grid, int block,
-                           cudaStream_t s);
+// minb: register budget sized for 1 or 2 blocks per SM; lanes: lanes of a
+// warp per node (2: implicit forms with minb 1 only)
+cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes,
+                               int* max_blocks_per_sm);
+cudaError_t launch_iterate(int form, int grad, int minb, int lanes, const IterArgs& a, int grid,
+                           int block, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched
 // Many registrations in one launch sequence.  Every per-kind array (pixels,

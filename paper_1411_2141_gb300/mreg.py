@@ -82,7 +82,8 @@ class mreg_options(C.Structure):
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
                 ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
                 ("smooth_passes", C.c_int32), ("host_topology", C.c_int32),
-                ("team_blocks_per_sm", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("team_blocks_per_sm", C.c_int32), ("node_lanes", C.c_int32),
+                ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -91,7 +92,8 @@ class mreg_stats_t(C.Structure):
                 ("max_pcg_iters", C.c_int32), ("not_converged", C.c_int32),
                 ("last_rel_resid", C.c_double), ("last_energy", C.c_double),
                 ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
-                ("device_status", C.c_int32), ("engine", C.c_int32)]
+                ("device_status", C.c_int32), ("engine", C.c_int32),
+                ("node_lanes", C.c_int32)]
 
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
@@ -212,7 +214,8 @@ def default_options() -> mreg_options:
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
                  coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0,
-                 smooth_passes=0, host_topology=False, allocator=None) -> mreg_options:
+                 smooth_passes=0, host_topology=False, node_lanes=0,
+                 allocator=None) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -229,6 +232,7 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.coeff_bf16 = int(bool(coeff_bf16))
     o.team_ctas = int(team_ctas)
     o.team_blocks_per_sm = int(team_blocks_per_sm)
+    o.node_lanes = int(node_lanes)
     o.smooth_passes = int(smooth_passes)
     o.host_topology = int(bool(host_topology))
     if allocator is not None:

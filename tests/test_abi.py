@@ -141,6 +141,14 @@ def test_option_validation_of_the_newer_fields(lib):
     _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, smooth_passes=65))
     _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S1", smooth_passes=2))
     _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, team_blocks_per_sm=3))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S1", node_lanes=3))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S0", node_lanes=2))
+    _expect(E.MREG_ERR_INVALID_ARG,
+            lambda: _create(V, T, img, img, mode="S1", node_lanes=2, team_blocks_per_sm=2))
+    _expect(E.MREG_ERR_INVALID_ARG,
+            lambda: _create(V, T, img, img, mode="S1", node_lanes=2, engine="cluster"))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: mreg.Batch([(V, T, img, img)], 0.1, 1.0, mode="S1",
+                                                       node_lanes=2))
     o = mreg.make_options(host_topology=True)
     assert o.host_topology == 1
     o.host_topology = 2
@@ -167,3 +175,12 @@ def test_options_struct_matches_the_header():
         r"^\s*(?:(?:int32_t|double|void\*)\s+(\w+);|void\*?\s*\(\*(\w+)\))", body, flags=re.M)]
     assert [n if n != "lambda" else "lambda_" for n in names] == \
         [f for f, _ in mreg.mreg_options._fields_]
+
+
+def test_stats_struct_matches_the_header():
+    """Every mreg_stats_t field of the header is in the binding's struct, in order."""
+    import re
+    text = open(os.path.join(ROOT, "include", "mreg.h")).read()
+    body = text[text.index("typedef struct {\n  int32_t iterations_done;"):text.index("} mreg_stats_t;")]
+    names = re.findall(r"^\s*(?:int32_t|double)\s+(\w+);", body, flags=re.M)
+    assert names == [f for f, _ in mreg.mreg_stats_t._fields_]

@@ -464,3 +464,47 @@ def test_energy_terms_of_eq1(mreg, c0, mode, grad, quad):
     assert abs(d - d_ref) <= 1e-5 * d_ref
     assert abs(sm - s_ref) <= 1e-6 * s_ref + 1e-12
     assert e == pytest.approx(d + c0.spec.alpha * sm, rel=1e-15)
+
+
+@pytest.mark.parametrize("mode,grad,quad", [m for m in MODES if m[0] != "S0"])
+def test_two_lanes_per_node(mreg, c0, mode, grad, quad):
+    """The implicit forms with each node's neighbour and incidence lists split
+    between two lanes (the automatic choice when one node per lane pair fits
+    the grid) and with one lane per node: both within the FP32 tolerances of
+    the oracle, and equal to each other up to summation order."""
+    n = 30
+    pb = _oracle(c0, mode, grad, quad)
+    u_ref, _ = pb.run(n)
+    msd_ref = pb.msd(u_ref)
+    out = {}
+    for lanes in (1, 2):
+        with _reg(mreg, c0, mode, grad, quad, engine="grid", node_lanes=lanes) as r:
+            r.step(n)
+            out[lanes] = (r.get_u(), r.msd(), r.stats())
+    assert out[1][2]["node_lanes"] == 1 and out[2][2]["node_lanes"] == 2
+    assert out[2][2]["block_size"] == 512
+    for lanes in (1, 2):
+        u, msd, _ = out[lanes]
+        assert np.abs(u - u_ref).max() <= U_TOL
+        assert abs(msd - msd_ref) / msd_ref <= MSD_RTOL
+    assert np.abs(out[1][0] - out[2][0]).max() <= 1e-5
+    with _reg(mreg, c0, mode, grad, quad) as r:
+        assert r.stats()["node_lanes"] == 2
+
+
+def test_automatic_lanes_follow_the_mesh_size(mreg):
+    """More than 256 nodes per SM: one lane per node, blocks of 512; the
+    explicit mode always runs one lane per node."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    side = int(np.ceil(np.sqrt(sms * 256 + 1))) + 1   # side^2 nodes > 256 per SM
+    ys, xs = np.mgrid[0:side, 0:side]
+    V = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.float32)
+    idx = (ys * side + xs)[:-1, :-1].ravel()
+    T = np.concatenate([np.stack([idx, idx + 1, idx + side + 1], 1),
+                        np.stack([idx, idx + side + 1, idx + side], 1)]).astype(np.int32)
+    img = np.zeros((side, side), np.float32)
+    with mreg.Registration(V, T, img, img, 0.1, 1.0, mode="S1") as r:
+        st = r.stats()
+        assert st["node_lanes"] == 1 and st["block_size"] == 512
+    with mreg.Registration(V, T, img, img, 0.1, 1.0, mode="S0") as r:
+        assert r.stats()["node_lanes"] == 1
