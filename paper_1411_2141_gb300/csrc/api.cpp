@@ -303,6 +303,7 @@ struct mreg_handle {
   double* pcg_res_hist = nullptr;
   float* warp_part = nullptr;
   float4* aff = nullptr;   // per-triangle affine records of the warp
+  float2* u_keep = nullptr;   // set by mreg_unroll_grad around its forward run
   double* msd = nullptr;
   int* counters = nullptr;   // [0] uncovered pixels, [1] non-finite values
 
@@ -343,6 +344,7 @@ struct mreg_handle {
     a.cTe16 = cTe16;
     a.ReV = ReV;
     a.ReQ = ReQ;
+    a.u_keep = u_keep ? u_keep + (size_t)it0 * nV : nullptr;
     a.u = u;
     a.f = f;
     a.F = F;
@@ -845,8 +847,10 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   if (n_iters < 0 || n_iters > 100000) return fail(MREG_ERR_INVALID_ARG, "n_iters out of range");
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
+  // states u_0 .. u_{K-1} densely (K x nV float2), then three vectors
   const size_t vec = align_up(sizeof(float2) * h->nV);
-  const size_t need = vec * ((size_t)n_iters + 3);
+  const size_t states = align_up(sizeof(float2) * h->nV * (size_t)n_iters);
+  const size_t need = states + 3 * vec;
   if (need > h->unroll_bytes) {
     CK(cudaStreamSynchronize(s), "synchronize");
     h->mem.put(h->unroll_buf, stream);
@@ -857,15 +861,26 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
     h->unroll_bytes = need;
   }
   char* base = (char*)h->unroll_buf;
-  float2* va = (float2*)(base + vec * n_iters);
-  float2* vb = (float2*)(base + vec * (n_iters + 1));
-  float2* vc = (float2*)(base + vec * (n_iters + 2));
-  // forward: u_0 .. u_{K-1} kept, the handle's iteration runs one step at a time
+  float2* const ustates = (float2*)base;
+  float2* va = (float2*)(base + states);
+  float2* vb = (float2*)(base + states + vec);
+  float2* vc = (float2*)(base + states + 2 * vec);
+  // forward: u_0 .. u_{K-1} kept.  The grid engine's iteration kernel stores
+  // each iteration's starting state itself (one launch per 1024 iterations);
+  // the cluster engine runs one step per launch after a copy of the state.
   CK(cudaMemcpyAsync(h->u, u0_dev, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s), "copy u0");
-  for (int k = 0; k < n_iters; ++k) {
-    CK(cudaMemcpyAsync(base + vec * k, h->u, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s),
-       "copy state");
-    mreg_status st = mreg_step(h, 1, stream);
+  if (h->engine == MREG_ENGINE_CLUSTER) {
+    for (int k = 0; k < n_iters; ++k) {
+      CK(cudaMemcpyAsync(ustates + (size_t)k * h->nV, h->u, sizeof(float2) * h->nV,
+                         cudaMemcpyDeviceToDevice, s),
+         "copy state");
+      mreg_status st = mreg_step(h, 1, stream);
+      if (st) return st;
+    }
+  } else if (n_iters > 0) {
+    h->u_keep = ustates;
+    const mreg_status st = mreg_step(h, n_iters, stream);
+    h->u_keep = nullptr;
     if (st) return st;
   }
   mreg_status st = mreg_warp_energy_grad(h, (const float*)h->u, energy_dev,
@@ -889,7 +904,7 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
       CK(mreg::launch_unroll_smooth_t(a, va, vc, s), "adjoint smoothing launch");
       std::swap(va, vc);
     }
-    CK(mreg::launch_unroll_adjoint_step(a, (const float2*)(base + vec * k), va, vb, s),
+    CK(mreg::launch_unroll_adjoint_step(a, ustates + (size_t)k * h->nV, va, vb, s),
        "adjoint step launch");
     std::swap(va, vb);
   }

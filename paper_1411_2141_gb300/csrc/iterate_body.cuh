@@ -319,8 +319,10 @@ __device__ __forceinline__ bool run_explicit(const IterArgs& a, TEAM& team, unsi
       src = dst;
     }
     ff e = ff_zero();
+    float2* keep = a.u_keep ? a.u_keep + (size_t)it * nV : nullptr;
     FOR_NODES(i, cached) {
       const float2 un = smooth_node(a, T, cached, src, i, lam);
+      if (keep) keep[i] = a.u[i];   // u at the start of this iteration
       a.u[i] = un;
       float2 Fv;
       e = ff_add_f(e, sample_node<kFormExplicit, GRAD>(a, i, un, a.f + i, Fn + i, &Fv));

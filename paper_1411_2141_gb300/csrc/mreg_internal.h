@@ -60,6 +60,8 @@ struct IterArgs {
   float2* F;             // force, two buffers of nV (iteration parity)
   float2* u0;            // S0: u - tau F, two buffers of nV (iteration parity)
   float2* us;            // S0: scratch of the repeated smoothing passes (nV)
+  float2* u_keep;        // S0 (grid engine): when set, u at the start of each iteration
+                         // of the launch, (n_iters x nV), for the unrolled adjoint
   float2* hq;            // edge form: per-edge force contribution
   float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s}
   float2* rt;            // true residual (FP32 copy) for restarts
