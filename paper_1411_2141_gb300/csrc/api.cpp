@@ -899,13 +899,11 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   a.cTe16 = h->cTe16;
   a.ReV = h->ReV;
   const int passes = h->opts.smooth_passes > 0 ? h->opts.smooth_passes : 1;
-  for (int k = n_iters - 1; k >= 0; --k) {
-    for (int p = 1; p < passes; ++p) {   // the repeated passes' S^T, then the fused step
-      CK(mreg::launch_unroll_smooth_t(a, va, vc, s), "adjoint smoothing launch");
-      std::swap(va, vc);
-    }
-    CK(mreg::launch_unroll_adjoint_step(a, ustates + (size_t)k * h->nV, va, vb, s),
-       "adjoint step launch");
+  CK(mreg::launch_unroll_adjoint(a, ustates, n_iters, passes, va, vb, vc, h->bar, h->status,
+                                 h->num_sms, s),
+     "adjoint launch");
+  for (int k = n_iters - 1; k >= 0; --k) {   // the kernel's rotation of the buffers
+    for (int p = 1; p < passes; ++p) std::swap(va, vc);
     std::swap(va, vb);
   }
   CK(cudaMemcpyAsync(grad_dev, va, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s),

@@ -141,10 +141,15 @@ struct UnrollArgs {
   const __nv_bfloat16* cTe16;
   const float* ReV;
 };
-cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
-                                       float2* vout, cudaStream_t s);
-cudaError_t launch_unroll_smooth_t(const UnrollArgs& a, const float2* vin, float2* vout,
-                                   cudaStream_t s);
+// The adjoint recursion of an unrolled run of n_iters explicit iterations:
+// va holds dE/du_K on entry; the three buffers rotate (passes - 1 smoothing
+// passes and one fused step per iteration, each swapping the input with its
+// output buffer), so the caller replays the rotation to find dE/du_0.  One
+// cooperative launch with grid barriers on bar (zeroed here) and status.
+cudaError_t launch_unroll_adjoint(const UnrollArgs& a, const float2* ustates, int n_iters,
+                                  int passes, float2* va, float2* vb, float2* vc,
+                                  unsigned long long* bar, int* status, int num_sms,
+                                  cudaStream_t s);
 
 // Warp energy 1/2 sum (R - Re)^2 at a.u and its gradient with respect to the
 // node displacements (rg: W*H scratch, tpart: 3*nT scratch).

@@ -15,6 +15,7 @@
 // difference with Re, accumulated per thread, reduced per block by warp
 // shuffles in a fixed order, then over blocks in a fixed order; the sums
 // are float-float (hi + lo FP32 pairs), the final mean FP64.
+#include <algorithm>
 #include <climits>
 
 #include "setup_common.cuh"
@@ -246,75 +247,95 @@ __global__ void k_warp_grad_nodes(const int* __restrict__ inc_ptr, const int* __
   }
 }
 
-// One adjoint step of an explicit (S0) iteration with the spline gradient:
+// One adjoint step of an explicit (S0) iteration with the spline gradient,
+// at node j:
 //   v_out = (I - tau D(u_k)) S^T v_in,  S = (1 - l) I + l A^Lap (Eq. 5, 14),
 //   D_j = grad Te grad Te^T + r_j Hess Te at V_j + u_k,j (the Jacobian of
 //   F_j = r_j grad Te(V_j + u_j)),
 // with (A^Lap^T v)_j = sum_{i in N1(j)} v_i / m_i (the 1-ring is symmetric).
-__global__ void k_unroll_adjoint_step(const UnrollArgs a, const float2* __restrict__ uk,
-                                      const float2* __restrict__ vin, float2* __restrict__ vout) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.nV; j += gridDim.x * blockDim.x) {
-    const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
-    float sx = 0.0f, sy = 0.0f;
-    for (int k = beg; k < end; ++k) {
-      const int i = __ldg(a.adj_col + k);
-      const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
-      const float2 vi = vin[i];
-      sx += vi.x / mi;
-      sy += vi.y / mi;
-    }
-    const float2 vj = vin[j];
-    const float wx = (1.0f - a.lam) * vj.x + a.lam * sx;
-    const float wy = (1.0f - a.lam) * vj.y + a.lam * sy;
-    const float2 V = __ldg(a.V + j), u = uk[j];
-    int bx, by;
-    float ox, oy;
-    split_coord(V.x, bx, ox);
-    split_coord(V.y, by, oy);
-    float f, gx, gy, hxx, hxy, hyy;
-    if (a.cTe16)
-      spline_sample_hessian(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
-    else
-      spline_sample_hessian(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
-    const float r = f - __ldg(a.ReV + j);
-    const float d00 = gx * gx + r * hxx, d01 = gx * gy + r * hxy, d11 = gy * gy + r * hyy;
-    vout[j] = make_float2(wx - a.tau * (d00 * wx + d01 * wy), wy - a.tau * (d01 * wx + d11 * wy));
+__device__ __forceinline__ float2 smooth_t_node(const UnrollArgs& a, const float2* vin, int j) {
+  const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
+  float sx = 0.0f, sy = 0.0f;
+  for (int k = beg; k < end; ++k) {
+    const int i = __ldg(a.adj_col + k);
+    const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
+    const float2 vi = vin[i];
+    sx += vi.x / mi;
+    sy += vi.y / mi;
   }
+  const float2 vj = vin[j];
+  return make_float2((1.0f - a.lam) * vj.x + a.lam * sx, (1.0f - a.lam) * vj.y + a.lam * sy);
 }
 
-// One transposed Eq. 14 pass: v_out = S^T v_in (the repeated passes of an
-// iteration with smooth_passes > 1 apply it before the fused step above).
-__global__ void k_unroll_smooth_t(const UnrollArgs a, const float2* __restrict__ vin,
-                                  float2* __restrict__ vout) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.nV; j += gridDim.x * blockDim.x) {
-    const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
-    float sx = 0.0f, sy = 0.0f;
-    for (int k = beg; k < end; ++k) {
-      const int i = __ldg(a.adj_col + k);
-      const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
-      const float2 vi = vin[i];
-      sx += vi.x / mi;
-      sy += vi.y / mi;
+__device__ __forceinline__ float2 adjoint_step_node(const UnrollArgs& a, const float2* uk,
+                                                    const float2* vin, int j) {
+  const float2 w = smooth_t_node(a, vin, j);
+  const float2 V = __ldg(a.V + j), u = uk[j];
+  int bx, by;
+  float ox, oy;
+  split_coord(V.x, bx, ox);
+  split_coord(V.y, by, oy);
+  float f, gx, gy, hxx, hxy, hyy;
+  if (a.cTe16)
+    spline_sample_hessian(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
+  else
+    spline_sample_hessian(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
+  const float r = f - __ldg(a.ReV + j);
+  const float d00 = gx * gx + r * hxx, d01 = gx * gy + r * hxy, d11 = gy * gy + r * hyy;
+  return make_float2(w.x - a.tau * (d00 * w.x + d01 * w.y), w.y - a.tau * (d01 * w.x + d11 * w.y));
+}
+
+// The whole adjoint recursion of an unrolled run in one cooperative launch:
+// for k = K-1 .. 0, (smooth_passes - 1) transposed Eq. 14 passes and then the
+// fused step above, a grid barrier after each (a node reads its neighbours'
+// v of the previous pass).  The buffers rotate as on the host, which knows
+// where the result ends.
+constexpr int kUnrollBlock = 256;
+
+__global__ void __launch_bounds__(kUnrollBlock) k_unroll_adjoint(
+    const UnrollArgs a, const float2* __restrict__ ustates, int n_iters, int passes, float2* va,
+    float2* vb, float2* vc, unsigned long long* bar, int* status) {
+  __shared__ int s_flag;
+  GridBarrier gb{bar, status, (unsigned long long)gridDim.x, 0ull};
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int k = n_iters - 1; k >= 0; --k) {
+    for (int p = 1; p < passes; ++p) {
+      for (int j = tid; j < a.nV; j += nth) vc[j] = smooth_t_node(a, va, j);
+      if (!gb.sync(&s_flag)) return;
+      float2* t = va;
+      va = vc;
+      vc = t;
     }
-    const float2 vj = vin[j];
-    vout[j] = make_float2((1.0f - a.lam) * vj.x + a.lam * sx, (1.0f - a.lam) * vj.y + a.lam * sy);
+    const float2* uk = ustates + (size_t)k * a.nV;
+    for (int j = tid; j < a.nV; j += nth) vb[j] = adjoint_step_node(a, uk, va, j);
+    if (k > 0 && !gb.sync(&s_flag)) return;   // the launch's end orders the last step
+    float2* t = va;
+    va = vb;
+    vb = t;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_unroll_smooth_t(const UnrollArgs& a, const float2* vin, float2* vout,
-                                   cudaStream_t s) {
-  const int g = (a.nV + 255) / 256 < 8192 ? (a.nV + 255) / 256 : 8192;
-  if (a.nV > 0) k_unroll_smooth_t<<<g, 256, 0, s>>>(a, vin, vout);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_unroll_adjoint_step(const UnrollArgs& a, const float2* uk, const float2* vin,
-                                       float2* vout, cudaStream_t s) {
-  const int g = (a.nV + 255) / 256 < 8192 ? (a.nV + 255) / 256 : 8192;
-  if (a.nV > 0) k_unroll_adjoint_step<<<g, 256, 0, s>>>(a, uk, vin, vout);
-  return cudaGetLastError();
+cudaError_t launch_unroll_adjoint(const UnrollArgs& a, const float2* ustates, int n_iters,
+                                  int passes, float2* va, float2* vb, float2* vc,
+                                  unsigned long long* bar, int* status, int num_sms,
+                                  cudaStream_t s) {
+  if (n_iters <= 0 || a.nV <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unroll_adjoint,
+                                                                kUnrollBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t want = ((int64_t)a.nV + kUnrollBlock - 1) / kUnrollBlock;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)per_sm * num_sms);
+  e = cudaMemsetAsync(bar, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  UnrollArgs ca = a;
+  void* args[] = {(void*)&ca, (void*)&ustates, (void*)&n_iters, (void*)&passes,
+                  (void*)&va, (void*)&vb, (void*)&vc, (void*)&bar, (void*)&status};
+  return cudaLaunchCooperativeKernel((void*)k_unroll_adjoint, dim3(grid), dim3(kUnrollBlock), args,
+                                     0, s);
 }
 
 cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tpart,
