@@ -211,18 +211,27 @@ __global__ void k_warp_grad_tris(const float2* __restrict__ V, const int* __rest
     const int y1 = min(H - 1, (int)floorf(fmaxf(A.y, fmaxf(B.y, C.y))));
     float2 ga = make_float2(0.0f, 0.0f), gb = ga, gc = ga;
     for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const int64_t p = (int64_t)y * W + x;
-        if (__ldg(pix + p) != t) continue;
-        const float2 q = __ldg(rg + p);
-        float la, lb, lc;
-        pixel_barycentric(A, B, C, x, y, la, lb, lc);
-        ga.x += la * q.x;
-        ga.y += la * q.y;
-        gb.x += lb * q.x;
-        gb.y += lb * q.y;
-        gc.x += lc * q.x;
-        gc.y += lc * q.y;
+      for (int x0r = x0; x0r <= x1; x0r += 4) {   // four pixels' loads in flight, then in order
+        int own[4];
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t p = (int64_t)y * W + min(x0r + u, x1);
+          own[u] = __ldg(pix + p);
+          q[u] = __ldg(rg + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (x0r + u > x1 || own[u] != t) continue;
+          float la, lb, lc;
+          pixel_barycentric(A, B, C, x0r + u, y, la, lb, lc);
+          ga.x += la * q[u].x;
+          ga.y += la * q[u].y;
+          gb.x += lb * q[u].x;
+          gb.y += lb * q[u].y;
+          gc.x += lc * q[u].x;
+          gc.y += lc * q[u].y;
+        }
       }
     tpart[3 * (size_t)t] = ga;
     tpart[3 * (size_t)t + 1] = gb;
@@ -236,12 +245,27 @@ __global__ void k_warp_grad_nodes(const int* __restrict__ inc_ptr, const int* __
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += gridDim.x * blockDim.x) {
     float gx = 0.0f, gy = 0.0f;
     const int e = __ldg(inc_ptr + i + 1);
-    for (int k = __ldg(inc_ptr + i); k < e; ++k) {
-      const int t = __ldg(inc_tri + k);
-      const int corner = __ldg(tri + 3 * t) == i ? 0 : (__ldg(tri + 3 * t + 1) == i ? 1 : 2);
-      const float2 q = __ldg(tpart + 3 * (size_t)t + corner);
-      gx += q.x;
-      gy += q.y;
+    for (int k0 = __ldg(inc_ptr + i); k0 < e; k0 += 4) {   // four triangles at a time, in order
+      int t[4], c0[4], c1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u] = __ldg(inc_tri + min(k0 + u, e - 1));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c0[u] = __ldg(tri + 3 * t[u]);
+        c1[u] = __ldg(tri + 3 * t[u] + 1);
+      }
+      float2 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int corner = c0[u] == i ? 0 : (c1[u] == i ? 1 : 2);
+        q[u] = __ldg(tpart + 3 * (size_t)t[u] + corner);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k0 + u >= e) continue;
+        gx += q[u].x;
+        gy += q[u].y;
+      }
     }
     grad[i] = make_float2(gx, gy);
   }
@@ -253,15 +277,29 @@ __global__ void k_warp_grad_nodes(const int* __restrict__ inc_ptr, const int* __
 //   D_j = grad Te grad Te^T + r_j Hess Te at V_j + u_k,j (the Jacobian of
 //   F_j = r_j grad Te(V_j + u_j)),
 // with (A^Lap^T v)_j = sum_{i in N1(j)} v_i / m_i (the 1-ring is symmetric).
+// The neighbours are gathered four at a time (their loads in flight
+// together) and summed in list order.
 __device__ __forceinline__ float2 smooth_t_node(const UnrollArgs& a, const float2* vin, int j) {
   const int beg = __ldg(a.adj_ptr + j), end = __ldg(a.adj_ptr + j + 1);
   float sx = 0.0f, sy = 0.0f;
-  for (int k = beg; k < end; ++k) {
-    const int i = __ldg(a.adj_col + k);
-    const float mi = (float)(__ldg(a.adj_ptr + i + 1) - __ldg(a.adj_ptr + i));
-    const float2 vi = vin[i];
-    sx += vi.x / mi;
-    sy += vi.y / mi;
+  for (int k0 = beg; k0 < end; k0 += 4) {
+    int i[4], p0[4], p1[4];
+    float2 vi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) i[u] = k0 + u < end ? __ldg(a.adj_col + k0 + u) : j;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      p0[u] = __ldg(a.adj_ptr + i[u]);
+      p1[u] = __ldg(a.adj_ptr + i[u] + 1);
+      vi[u] = vin[i[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u >= end) continue;
+      const float mi = (float)(p1[u] - p0[u]);
+      sx += vi[u].x / mi;
+      sy += vi[u].y / mi;
+    }
   }
   const float2 vj = vin[j];
   return make_float2((1.0f - a.lam) * vj.x + a.lam * sx, (1.0f - a.lam) * vj.y + a.lam * sy);
