@@ -284,6 +284,10 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 PROFILE_C1 = ("k_implicit_512px_20k_nodes.md",
               ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "iterate.cu",
                "mreg_internal.h"])
+PROFILE_C2 = ("k_implicit_2048px_250k_nodes.md",
+              ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "iterate.cu",
+               "mreg_internal.h"])
+PROFILE_ONE_PAIR = {1: PROFILE_C1, 2: PROFILE_C2}
 PROFILE_C3 = ("k_batch_256_uneven_pairs.md",
               ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "batch.cu",
                "setup_common.cuh", "mreg_internal.h"])
@@ -439,9 +443,10 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak,
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": per_iter * n_iter,
-                     "traffic": (profiled_traffic(PROFILE_C1)
-                                 if (args.config, args.mode, args.grad, args.coeff)
-                                 == (1, "S1", "G0", "fp32") else None)},
+                     "traffic": (profiled_traffic(PROFILE_ONE_PAIR[args.config])
+                                 if args.config in PROFILE_ONE_PAIR
+                                 and (args.mode, args.grad, args.coeff) == ("S1", "G0", "fp32")
+                                 else None)},
         "clocks": clk,
         "gpu_launches": launches_per_registration(args, n_iter) * args.steps,
         "launch": {"grid": st["grid_blocks"], "block": st["block_size"]},
