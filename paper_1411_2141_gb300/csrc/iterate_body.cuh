@@ -688,16 +688,10 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
         gam[c] = gn;
       }
       if (restart && verify) {
-        // Restart every unconverged component from the true residual,
-        // r = rt, z = D^-1 rt, and form w = A z of the restarted state in the
-        // same phase: a node takes its neighbours' new z from their rt
-        // (written by the verify step, stable here) with the owners' own
-        // expression, and their old z (not rewritten) for a converged
-        // component.  One reduction gives gamma = r.z and delta = w.z.
-        float c4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        FOR_NODES(i, cached) {
-          int beg, deg;
-          T.arow(a, cached, i, beg, deg);
+        // restart every unconverged component from the true residual:
+        // r = rt, z = D^-1 rt; w = A z is formed by the next need_w pass
+        float c2[2] = {0.0f, 0.0f};
+        for (int i = tid; i < nV; i += nth) {
           float4* node = cg[q] + 3 * (size_t)i;
           const float2 rt = a.rt[i];
           float4 xz = node[0], pr = node[1];
@@ -710,59 +704,21 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
             pr.w = rt.y;
             xz.w = __fmul_rn(di, rt.y);
           }
-          const float ad = a_diag<FORM>(a, i, deg);
-          float wx = nl.lead() ? ad * xz.z : 0.0f, wy = nl.lead() ? ad * xz.w : 0.0f;
-          for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
-            int jj[4];
-            float dd[4];
-            float2 rj[4];
-            float4 xj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const bool ok = k0 + u < deg;
-              jj[u] = ok ? T.adj(a, cached, beg, k0 + u) : i;
-              dd[u] = ok ? T.dj(a, cached, jj[u], k0 + u) : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              rj[u] = a.rt[jj[u]];
-              xj[u] = cg[q][3 * (size_t)jj[u]];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (k0 + u >= deg) continue;
-              const float zx = conv[0] ? xj[u].z : __fmul_rn(dd[u], rj[u].x);
-              const float zy = conv[1] ? xj[u].w : __fmul_rn(dd[u], rj[u].y);
-              const float ao = a_off<FORM>(a, beg + k0 + u);
-              wx = __fmaf_rn(ao, zx, wx);
-              wy = __fmaf_rn(ao, zy, wy);
-            }
-          }
-          wx = nl.sum(wx);
-          wy = nl.sum(wy);
-          if (!nl.lead()) continue;
-          node[0] = xz;   // a converged component keeps its bits
+          node[0] = xz;
           node[1] = pr;
-          node[2] = make_float4(wx, wy, 0.0f, 0.0f);
-          c4[0] += pr.z * xz.z;
-          c4[1] += pr.w * xz.w;
-          c4[2] += wx * xz.z;
-          c4[3] += wy * xz.w;
+          c2[0] += pr.z * xz.z;
+          c2[1] += pr.w * xz.w;
         }
-        block_record<4, false>(c4, ff_zero(), MY_REC, s_red);
+        block_record<2, false>(c2, ff_zero(), MY_REC, s_red);
         SYNC_OR_LEAVE();
         ff unused;
-        grid_totals<4, false>(ALL_REC, nb, c4, unused, s_tot + par * kRec);
+        grid_totals<2, false>(ALL_REC, nb, c2, unused, s_tot + par * kRec);
         par ^= 1;
-        gam[0] = c4[0];
-        gam[1] = c4[1];
+        gam[0] = c2[0];
+        gam[1] = c2[1];
         rr[0] = rt2[0];
         rr[1] = rt2[1];
-        step.alpha.x = (conv[0] || !(c4[2] > 0.0f)) ? 0.0f : gam[0] / c4[2];
-        step.alpha.y = (conv[1] || !(c4[3] > 0.0f)) ? 0.0f : gam[1] / c4[3];
-        step.beta = make_float2(0.0f, 0.0f);
-        step.first = true;
-        need_w = false;
+        need_w = true;
       } else if (restart) {
         // breakdown in the recursion without a true residual at hand: restart
         // from the recursive residual, which is the current r
