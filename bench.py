@@ -190,10 +190,11 @@ def run_reference(args, rank, world):
 def launches_per_registration(args, n_iter: int) -> int:
     """Our kernels in one timed step: prefilter (row and column pass) of Re
     and Te, [BF16 copy], Re at the nodes, [Re at edge midpoints], pixel map
-    (fill + scan), the persistent iteration kernel and its energy pass per
-    1024-iteration chunk, warp + MSD and the final MSD sum."""
+    (fill + map), the persistent iteration kernel and its energy pass per
+    1024-iteration chunk, the warp's per-triangle affine records, warp + MSD
+    and the final MSD sum."""
     chunks = (n_iter + 1023) // 1024
-    return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 2)
+    return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 3)
 
 
 def run_reference_adjoint(args):

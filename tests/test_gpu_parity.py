@@ -508,3 +508,32 @@ def test_automatic_lanes_follow_the_mesh_size(mreg):
         assert st["node_lanes"] == 1 and st["block_size"] == 512
     with mreg.Registration(V, T, img, img, 0.1, 1.0, mode="S0") as r:
         assert r.stats()["node_lanes"] == 1
+
+
+@pytest.mark.parametrize("hw", RAGGED)
+@pytest.mark.parametrize("amp", [0.7, 6.0])
+def test_warp_on_ragged_images(mreg, hw, amp):
+    """The warp + MSD against the oracle on images whose sides are not
+    multiples of the 32 x 16 tile, down to 2 x 2 (no 4 x 4 window inside the
+    image), with displacements that keep the taps inside (0.7 px) or push
+    many of them through the mirror extension (6 px)."""
+    H, W = hw
+    case = _ragged_case(H, W, seed=11)
+    x = case.V[:, 0].astype(np.float64)
+    y = case.V[:, 1].astype(np.float64)
+    u = (amp * np.stack([np.sin(x / 5.0 + 0.3), np.cos(y / 4.0 - 0.2)], 1)).astype(np.float32)
+    pb = _oracle(case)
+    R_ref = pb.warp(u.astype(np.float64))
+    msd_ref = pb.msd(u.astype(np.float64))
+    with _reg(mreg, case) as r:
+        r.set_u(u)
+        out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        msd_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+        r.warp(out, msd_dev)
+        torch.cuda.synchronize()
+        R = out.cpu().numpy()
+        msd = float(msd_dev.cpu()[0])
+        assert abs(r.msd() - msd) <= 1e-12 * msd + 1e-18   # the MSD-only instance
+    scale = max(1.0, float(np.abs(case.Te).max()))
+    assert np.abs(R - R_ref).max() <= 1e-5 * scale
+    assert abs(msd - msd_ref) <= 1e-5 * msd_ref + 1e-12
