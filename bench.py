@@ -441,7 +441,8 @@ def run_ours(args, rank, world, local_rank):
         "node_iters_per_s": value * case.n_nodes * n_iter,
         "msd": msd, "cg_iters_mean": cg_mean,
         "iteration_kernel_ms": it_ms,
-        "roofline": {"kernel": "k_iterate (persistent: sample + force + solve, all iterations)",
+        "roofline": {"kernel": ("k_explicit" if args.mode == "S0" else "k_implicit")
+                               + " (persistent: sample + force + update or solve, all iterations)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "peak_source": peak_src,
