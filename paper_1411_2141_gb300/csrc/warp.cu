@@ -305,20 +305,82 @@ __device__ __forceinline__ float2 smooth_t_node(const UnrollArgs& a, const float
   return make_float2((1.0f - a.lam) * vj.x + a.lam * sx, (1.0f - a.lam) * vj.y + a.lam * sy);
 }
 
+// The 16 coefficients around V_j + u_j and the fractions, loaded before the
+// neighbour gather of the step so that the two load chains overlap; the sums
+// are those of spline_sample_hessian, in its order.
+struct HessTaps {
+  float c[4][4];
+  float tx, ty;
+};
+
+template <class C>
+__device__ __forceinline__ void hessian_taps(const C* __restrict__ c, int W, int H, int bx, int by,
+                                             float ox, float oy, HessTaps& t) {
+  ox = fminf(fmaxf(ox, -1.0e7f), 1.0e7f);
+  oy = fminf(fmaxf(oy, -1.0e7f), 1.0e7f);
+  const float fx = floorf(ox), fy = floorf(oy);
+  const int ix = bx + (int)fx, iy = by + (int)fy;
+  t.tx = ox - fx;
+  t.ty = oy - fy;
+  int xs[4], ys[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    xs[k] = mirror_fold(ix - 1 + k, W);
+    ys[k] = mirror_fold(iy - 1 + k, H);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const C* row = c + (size_t)ys[m] * W;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t.c[m][k] = load_coef(row + xs[k]);
+  }
+}
+
+__device__ __forceinline__ void hessian_from_taps(const HessTaps& t, float& v, float& gx, float& gy,
+                                                  float& hxx, float& hxy, float& hyy) {
+  float wx[4], wy[4], dx[4], dy[4], ex[4], ey[4];
+  cubic_weights(t.tx, wx);
+  cubic_weights(t.ty, wy);
+  cubic_dweights(t.tx, dx);
+  cubic_dweights(t.ty, dy);
+  cubic_d2weights(t.tx, ex);
+  cubic_d2weights(t.ty, ey);
+  v = gx = gy = hxx = hxy = hyy = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float sw = 0.0f, sd = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sw += wx[k] * t.c[m][k];
+      sd += dx[k] * t.c[m][k];
+      se += ex[k] * t.c[m][k];
+    }
+    v += wy[m] * sw;
+    gx += wy[m] * sd;
+    gy += dy[m] * sw;
+    hxx += wy[m] * se;
+    hxy += dy[m] * sd;
+    hyy += ey[m] * sw;
+  }
+}
+
 __device__ __forceinline__ float2 adjoint_step_node(const UnrollArgs& a, const float2* uk,
                                                     const float2* vin, int j) {
-  const float2 w = smooth_t_node(a, vin, j);
   const float2 V = __ldg(a.V + j), u = uk[j];
   int bx, by;
   float ox, oy;
   split_coord(V.x, bx, ox);
   split_coord(V.y, by, oy);
-  float f, gx, gy, hxx, hxy, hyy;
+  HessTaps taps;
   if (a.cTe16)
-    spline_sample_hessian(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
+    hessian_taps(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, taps);
   else
-    spline_sample_hessian(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, f, gx, gy, hxx, hxy, hyy);
-  const float r = f - __ldg(a.ReV + j);
+    hessian_taps(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, taps);
+  const float rv = __ldg(a.ReV + j);
+  const float2 w = smooth_t_node(a, vin, j);
+  float f, gx, gy, hxx, hxy, hyy;
+  hessian_from_taps(taps, f, gx, gy, hxx, hxy, hyy);
+  const float r = f - rv;
   const float d00 = gx * gx + r * hxx, d01 = gx * gy + r * hxy, d11 = gy * gy + r * hyy;
   return make_float2(w.x - a.tau * (d00 * w.x + d01 * w.y), w.y - a.tau * (d01 * w.x + d11 * w.y));
 }
