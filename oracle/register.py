@@ -14,7 +14,7 @@ One iteration (Algorithm 1):
      directly; the oracle solves it with a sparse direct LU factorisation
      (``scipy.sparse.linalg.splu``), computed once per mesh.
 
-Readings of the paper adopted here (each is also listed in the design doc):
+Readings of the paper adopted here:
   * A1 (Eq. 2-4, 6 disagree on which image moves): the template moves.
     r_i = Te(V_i + u_i) - Re(V_i) with Re(V_i) fixed, F_i = r_i grad Te.
     This is the reading under which Eq. 6 is the gradient of Eq. 4.
