@@ -14,10 +14,18 @@ uneven size (sides 96-768, 500-40k nodes, 100 iterations each) in one CUDA
 graph launch around one persistent kernel, with the team shape chosen by the
 library's autotuner before timing.
 
---impl reference times the FP64 CPU oracle on the host cores instead (a
-bounded sample of each registration, extrapolated to the full iteration
-count).  Under torchrun (N > 1) every rank registers its own pairs on its
-own GPU (independent replicas, weak scaling); rank 0 prints one JSON line.
+The default run (config 1) also times the other forms briefly and reports
+them under "forms": the batched engine on the 256-pair workload (FP32 and
+BF16-stored coefficients), the same pairs through one-pair handles on 8 CUDA
+streams (the plain FP32 form), and the differentiation form (--no-forms
+skips them).  Its line carries "parity": the timed run's final node
+displacements and MSD against one full FP64 oracle registration of the same
+pair.
+
+--impl reference times the FP64 CPU oracle on the host cores instead: each
+timed step is one whole registration (all iterations) of the same pair.
+Under torchrun (N > 1) every rank registers its own pairs on its own GPU
+(independent replicas, weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -67,6 +75,9 @@ def parse():
                    help="differentiation form and --single: CUDA streams the pairs are spread over")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="config 1: skip the short runs of the batched, plain-on-streams and "
+                        "differentiation forms")
     return p.parse_args()
 
 
@@ -147,19 +158,40 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU side
-def oracle_registration_time(case, mode: str, grad: str, sample_iters: int = 20):
-    """Seconds of one registration by the FP64 oracle: set-up, a bounded run
-    of sample_iters iterations extrapolated to the full count, and the MSD."""
+def oracle_registration(case, mode: str, grad: str, n_iter: int | None = None):
+    """One whole registration by the FP64 oracle (set-up, n_iter iterations,
+    default the workload's full count, and the MSD): (seconds, u, MSD)."""
     from oracle import register
     t0 = time.perf_counter()
     pb = register.Problem(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau, mode, grad)
-    t1 = time.perf_counter()
-    u, _ = pb.run(sample_iters)
-    t2 = time.perf_counter()
-    pb.msd(u)
-    t3 = time.perf_counter()
-    n = case.spec.n_iter
-    return (t1 - t0) + (t2 - t1) * n / sample_iters + (t3 - t2), sample_iters
+    u, _ = pb.run(case.spec.n_iter if n_iter is None else n_iter)
+    msd = pb.msd(u)
+    return time.perf_counter() - t0, u, msd
+
+
+def host_cpu() -> dict:
+    """The host cores the oracle runs on (it uses one of them)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
+def parity_against_oracle(u, msd, u_ref, msd_ref, u_tol: float = 1e-4, msd_rtol: float = 1e-5) -> dict:
+    """Node displacements and MSD of a GPU run against the FP64 oracle's."""
+    du = float(np.abs(np.asarray(u, np.float64) - u_ref).max())
+    dm = float(abs(msd - msd_ref) / msd_ref)
+    return {"max_du_px": du, "msd_rel": dm, "u_tol_px": u_tol, "msd_rtol": msd_rtol,
+            "pass": bool(du <= u_tol and dm <= msd_rtol)}
 
 
 def run_reference(args, rank, world):
@@ -171,11 +203,11 @@ def run_reference(args, rank, world):
         return run_reference_adjoint(args)
     spec = inputs.config_spec(args.config)
     case = inputs.make_case(spec)
-    for _ in range(args.warmup):
-        oracle_registration_time(case, args.mode, args.grad, sample_iters=2)
+    for _ in range(args.warmup):   # warm-up: set-up and a short run, untimed
+        oracle_registration(case, args.mode, args.grad, n_iter=2)
     times = []
     for _ in range(args.steps):
-        t, sample_iters = oracle_registration_time(case, args.mode, args.grad)
+        t, _, _ = oracle_registration(case, args.mode, args.grad)
         times.append(t)
     sec = sum(times)
     value = args.steps / sec
@@ -187,8 +219,9 @@ def run_reference(args, rank, world):
         "config": workload_config(args, case),
         "node_iters_per_s": value * case.n_nodes * spec.n_iter,
         "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: full set-up + {sample_iters} of {spec.n_iter} "
-                                   f"iterations (time scaled x{spec.n_iter / sample_iters:g}) + MSD"},
+                         "host": host_cpu(),
+                         "sample": f"per step: one whole registration (set-up, all {spec.n_iter} "
+                                   f"iterations, MSD), numpy/scipy FP64, 1 thread"},
         "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -238,24 +271,24 @@ def run_reference_batch(args):
     cases = batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     for _ in range(args.warmup):
-        oracle_registration_time(cases[0], args.mode, args.grad, sample_iters=2)
-    total, pick, si = 0.0, None, None
+        oracle_registration(cases[0], args.mode, args.grad, n_iter=2)
+    measured, est, pick = 0.0, 0.0, None
     for _ in range(args.steps):
-        t, pick, si = oracle_batch_time(cases, args.mode, args.grad, n_sample_pairs=4,
-                                        sample_iters=5)
-        total += t
-    value = args.steps * len(cases) / total
-    sample = (f"per step: {len(pick)} of {len(cases)} pairs spread over the size range, set-up + "
-              f"{si} of {n_iter} iterations (scaled x{n_iter / si:g}) + MSD each, scaled to the "
-              f"batch by node count")
+        t, t_all, pick = oracle_batch_time(cases, args.mode, args.grad, n_sample_pairs=4)
+        measured += t
+        est += t_all
+    value = args.steps * len(cases) / est
+    sample = (f"per step: whole registrations ({n_iter} iterations) of {len(pick)} of the "
+              f"{len(cases)} pairs, spread over the size range; the rate per node applied to "
+              f"the whole batch (ms_per_step is the measured time of the sampled pairs)")
     line = {
         "impl": "reference", "metric": "registrations/s", "value": value, "unit": "registrations/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * measured / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": batch_workload_config(args, cases),
         "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "host": host_cpu(), "sample": sample},
         "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -397,6 +430,7 @@ def run_ours(args, rank, world, local_rank):
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     msd = float(msd_dev.item())
     st = reg.stats(stream)
+    u_gpu = reg.get_u(stream=stream)   # the last timed registration's result
 
     # end to end through the public API with host buffers (create from host
     # arrays, iterate, MSD and u back to the host, destroy)
@@ -433,7 +467,8 @@ def run_ours(args, rank, world, local_rank):
                            "allocator), set-up, iterations, MSD and u back to the host, destroy"}
 
     if rank != 0:
-        return
+        reg.close()
+        return None
     value = whole_job_rate(args.steps, world, total_s)
     e = np.sort(np.concatenate([case.T[:, [0, 1]], case.T[:, [1, 2]], case.T[:, [2, 0]]]), axis=1)
     nnz = 2 * len(np.unique(e, axis=0))          # off-diagonal entries of the node graph
@@ -441,6 +476,9 @@ def run_ours(args, rank, world, local_rank):
     it_ms = statistics.mean(iter_ms)
     achieved = per_iter * n_iter / (it_ms / 1e3) / 1e9
     peak, peak_src = peak_hbm()
+    traffic = (profiled_traffic(PROFILE_ONE_PAIR[args.config])
+               if args.config in PROFILE_ONE_PAIR
+               and (args.mode, args.grad, args.coeff) == ("S1", "G0", "fp32") else None)
     line = {
         "metric": "registrations/s", "value": value, "unit": "registrations/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -455,11 +493,13 @@ def run_ours(args, rank, world, local_rank):
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "peak_source": peak_src,
+                     "basis": "algorithmic bytes per launch / launch time, against the HBM copy "
+                              "peak; the working set is L2-resident at this size, so the kernel "
+                              "is bound by latency (grid barriers, dependent L2 round trips), "
+                              "not by DRAM",
                      "algorithmic_bytes_per_launch": per_iter * n_iter,
-                     "traffic": (profiled_traffic(PROFILE_ONE_PAIR[args.config])
-                                 if args.config in PROFILE_ONE_PAIR
-                                 and (args.mode, args.grad, args.coeff) == ("S1", "G0", "fp32")
-                                 else None)},
+                     "traffic": traffic,
+                     "dram_gbs": (traffic / (it_ms / 1e3) / 1e9 if traffic else None)},
         "clocks": clk,
         "gpu_launches": launches_per_registration(args, n_iter) * args.steps,
         "launch": {"grid": st["grid_blocks"], "block": st["block_size"]},
@@ -467,13 +507,19 @@ def run_ours(args, rank, world, local_rank):
     if e2e is not None:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        t_reg, sample_iters = oracle_registration_time(case, args.mode, args.grad)
+        # one whole oracle registration of the same pair: the timed CPU
+        # baseline, and the reference the timed GPU run is checked against
+        t_reg, u_ref, msd_ref = oracle_registration(case, args.mode, args.grad)
         line["cpu_baseline"] = {
             "value": 1.0 / t_reg, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-            "sample": f"one registration: full set-up + {sample_iters} of {n_iter} iterations "
-                      f"(time scaled x{n_iter / sample_iters:g}) + MSD, numpy/scipy FP64, 1 thread"}
-    print(json.dumps(line), flush=True)
+            "host": host_cpu(),
+            "sample": f"one whole registration (set-up, all {n_iter} iterations, MSD), "
+                      f"numpy/scipy FP64, 1 thread"}
+        line["parity"] = parity_against_oracle(u_gpu, msd, u_ref, msd_ref)
+        line["parity"]["what"] = ("final node displacements and MSD of the last timed "
+                                  "registration against the FP64 oracle's")
     reg.close()
+    return line
 
 # ---------------------------------------------------------- batched form
 BATCH_LAUNCHES = 9   # prefilter rows + columns, Re at nodes, pixel fill + map,
@@ -507,19 +553,20 @@ def batch_cases(n_pairs: int = 0):
     return inputs.make_cases(inputs.batched_specs(3, n_pairs or None))
 
 
-def oracle_batch_time(cases, mode: str, grad: str, n_sample_pairs: int = 8, sample_iters: int = 10):
-    """Seconds for the FP64 oracle to register the whole batch, estimated from
-    n_sample_pairs pairs spread over the size range (set-up, sample_iters of
-    the iterations scaled to the full count, MSD), scaled by total nodes."""
+def oracle_batch_time(cases, mode: str, grad: str, n_sample_pairs: int = 4):
+    """The FP64 oracle on the batched workload: whole registrations (all
+    iterations) of n_sample_pairs pairs spread over the size range.  Returns
+    the seconds they took, the seconds the whole batch would take at the same
+    rate per node, and the pairs picked."""
     order = np.argsort([c.n_nodes for c in cases])
-    pick = [int(order[round(k * (len(order) - 1) / (n_sample_pairs - 1))])
+    pick = [int(order[round(k * (len(order) - 1) / max(1, n_sample_pairs - 1))])
             for k in range(n_sample_pairs)]
-    t_pick = sum(oracle_registration_time(cases[k], mode, grad, sample_iters)[0] for k in pick)
+    t_pick = sum(oracle_registration(cases[k], mode, grad)[0] for k in pick)
     scale = sum(c.n_nodes for c in cases) / sum(cases[k].n_nodes for k in pick)
-    return t_pick * scale, pick, sample_iters
+    return t_pick, t_pick * scale, pick
 
 
-def run_ours_batch_single(args, rank, world, local_rank):
+def run_ours_batch_single(args, rank, world, local_rank, cases=None):
     """The batched workload through the one-pair engine: every pair has its
     own handle (created before timing); a step registers all pairs one after
     another (reset + iterations + warp/MSD each), as the plain FP32 form
@@ -530,7 +577,7 @@ def run_ours_batch_single(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     mreg.load()
-    cases = batch_cases(args.pairs)
+    cases = cases or batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
     regs = [mreg.Registration(c.V, c.T, torch.from_numpy(c.Re).to(dev),
@@ -574,7 +621,9 @@ def run_ours_batch_single(args, rank, world, local_rank):
     clk = clocks.stop()
     total_s = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, world, dev)
     if rank != 0:
-        return
+        for r in regs:
+            r.close()
+        return None
     value = whole_job_rate(args.steps * len(cases), world, total_s)
     cfg = batch_workload_config(args, cases)
     cfg["engine"] = ("one-pair grid engine, pairs in sequence (the plain FP32 form)"
@@ -590,19 +639,19 @@ def run_ours_batch_single(args, rank, world, local_rank):
         "msd_mean": float(msd_dev.double().mean().item()), "clocks": clk,
         "gpu_launches": sum(launches_per_registration(args, n_iter) for _ in cases) * args.steps,
     }
-    print(json.dumps(line), flush=True)
     for r in regs:
         r.close()
+    return line
 
 
-def run_ours_batch(args, rank, world, local_rank):
+def run_ours_batch(args, rank, world, local_rank, cases=None):
     import torch
     from paper_1411_2141_gb300 import mreg
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     mreg.load()
-    cases = batch_cases(args.pairs)
+    cases = cases or batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
     bf16 = args.coeff == "bf16"
@@ -693,7 +742,7 @@ def run_ours_batch(args, rank, world, local_rank):
                        "allocator), runs it, reads MSD and u, destroys it"}
     if rank != 0:
         b.close()
-        return
+        return None
     value = whole_job_rate(args.steps * len(cases), world, total_s)
     it_ms = statistics.mean(iter_ms)
     achieved = per_iter_total * n_iter / (it_ms / 1e3) / 1e9
@@ -725,14 +774,15 @@ def run_ours_batch(args, rank, world, local_rank):
     if e2e is not None:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        t_all, pick, si = oracle_batch_time(cases, args.mode, args.grad)
+        _, t_all, pick = oracle_batch_time(cases, args.mode, args.grad)
         line["cpu_baseline"] = {
             "value": len(cases) / t_all, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(pick)} of {len(cases)} pairs spread over the size range: set-up + "
-                      f"{si} of {n_iter} iterations (scaled x{n_iter / si:g}) + MSD each, "
-                      f"scaled to the batch by node count; numpy/scipy FP64, 1 thread"}
-    print(json.dumps(line), flush=True)
+            "host": host_cpu(),
+            "sample": f"whole registrations ({n_iter} iterations) of {len(pick)} of the "
+                      f"{len(cases)} pairs spread over the size range, the rate per node "
+                      f"applied to the whole batch; numpy/scipy FP64, 1 thread"}
     b.close()
+    return line
 
 # ------------------------------------------------- differentiation form
 def adjoint_cases(n_pairs: int = 0):
@@ -855,7 +905,9 @@ def run_ours_adjoint(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d + 8 * len(cases)),
                "steps": e2e_steps}
     if rank != 0:
-        return
+        for r in regs:
+            r.close()
+        return None
     value = whole_job_rate(args.steps * len(cases), world, total_s)
     fw_bytes = []
     for c in cases:
@@ -898,10 +950,62 @@ def run_ours_adjoint(args, rank, world, local_rank):
                                 "kind": "oracle",
                                 "sample": "one pair: set-up, 20 forward iterations and the adjoint "
                                           "recursion, numpy/scipy FP64, 1 thread"}
-    print(json.dumps(line), flush=True)
     for r in regs:
         r.close()
+    return line
 
+
+
+FORM_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "iteration_kernel_ms",
+             "cg_iters_mean", "msd_mean", "clocks", "gpu_launches")
+
+
+def _form_summary(line: dict, what: str) -> dict:
+    out = {"what": what}
+    out.update({k: line[k] for k in FORM_KEYS if k in line})
+    if "roofline" in line:
+        out["roofline"] = {k: line["roofline"][k] for k in ("kernel", "achieved", "frac", "peak")}
+    if "team" in line.get("config", {}):
+        out["team"] = line["config"]["team"]
+    return out
+
+
+def run_forms(args, rank, world, local_rank) -> dict | None:
+    """Short runs (3 warm-up and 3 timed steps each, L2 flushed between
+    steps) of the other forms, reported beside the one-pair line."""
+    import copy
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.no_cpu_baseline, sub.no_e2e, sub.pairs = 3, 3, True, True, 0
+    sub.mode, sub.grad, sub.coeff, sub.team, sub.teams = "S1", "G0", "fp32", None, 0
+    cases = batch_cases()
+    forms = {}
+    sub.config = 3
+    line = run_ours_batch(sub, rank, world, local_rank, cases)
+    if line is not None:
+        forms["batched_fp32"] = _form_summary(
+            line, "config 3: 256 uneven pairs, 100 iterations each, batched engine (one CUDA-graph "
+                  "launch, autotuned team shape), FP32")
+        sub.team = ",".join(str(x) for x in line["autotune"]["chosen"])
+    sub.coeff = "bf16"
+    line = run_ours_batch(sub, rank, world, local_rank, cases)
+    if line is not None:
+        forms["batched_bf16"] = _form_summary(
+            line, "the same batch with BF16-stored Te coefficients (the precision form), the team "
+                  "shape the FP32 run's autotuner chose")
+    sub.coeff, sub.team = "fp32", None
+    line = run_ours_batch_single(sub, rank, world, local_rank, cases)
+    if line is not None:
+        forms["plain_fp32_streams"] = _form_summary(
+            line, f"the same 256 pairs through one-pair handles (the plain FP32 form), pairs "
+                  f"spread over {sub.streams} CUDA streams")
+    del cases
+    sub.config = 4
+    line = run_ours_adjoint(sub, rank, world, local_rank)
+    if line is not None:
+        forms["differentiation"] = _form_summary(
+            line, "config 4: gradient of the warp energy through 20 unrolled explicit iterations, "
+                  f"64 pairs of 256x256, {sub.streams} CUDA streams")
+    return forms if rank == 0 else None
 
 
 def main():
@@ -918,13 +1022,19 @@ def main():
         torch.distributed.init_process_group("nccl")
     try:
         if args.config == 4:
-            run_ours_adjoint(args, rank, world, local_rank)
+            line = run_ours_adjoint(args, rank, world, local_rank)
         elif args.config == 3 and args.single:
-            run_ours_batch_single(args, rank, world, local_rank)
+            line = run_ours_batch_single(args, rank, world, local_rank)
         elif args.config == 3:
-            run_ours_batch(args, rank, world, local_rank)
+            line = run_ours_batch(args, rank, world, local_rank)
         else:
-            run_ours(args, rank, world, local_rank)
+            line = run_ours(args, rank, world, local_rank)
+            if args.config == 1 and not args.no_forms:
+                forms = run_forms(args, rank, world, local_rank)
+                if line is not None:
+                    line["forms"] = forms
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch

@@ -88,15 +88,12 @@ enum {
                                    needs MREG_GRAD_SPLINE                    */
 };
 
-/* Where the iteration loop runs. */
+/* Where the iteration loop of one pair runs (the batched engine is the
+ * mreg_batch_* API). */
 enum {
-  MREG_ENGINE_AUTO = 0,    /* the grid engine (measured faster on the 512^2 /
-                              20k-node workload)                              */
-  MREG_ENGINE_GRID = 1,    /* one persistent cooperative kernel over the GPU,
+  MREG_ENGINE_AUTO = 0,    /* the grid engine                                 */
+  MREG_ENGINE_GRID = 1     /* one persistent cooperative kernel over the GPU,
                               node state in global memory (any mesh size)      */
-  MREG_ENGINE_CLUSTER = 2  /* one thread-block cluster (<= 16 CTAs) holding the
-                              node state in distributed shared memory (meshes
-                              up to ~26k nodes; not the edge-midpoint form)    */
 };
 
 typedef struct mreg_handle mreg_handle;
@@ -128,8 +125,12 @@ typedef struct {
   int32_t quad;        /* MREG_QUAD_*                       (default NODES) */
   int32_t pcg_maxit;   /* CG iteration cap per solve, <= 10000 (default 100) */
   double lambda;       /* smoothing weight; < 0 means tau * alpha (default) */
-  double pcg_rtol;     /* stop when ||b - A u'||_2 <= rtol ||b||_2, residual
-                          formed in FP64, per component     (default 1e-7)  */
+  double pcg_rtol;     /* stop when ||b - A u'||_2 <= rtol ||b||_2 per
+                          component.  b and the residual b - A u' are
+                          formed in float-float (an FP32 hi + lo pair, a
+                          ~48-bit significand; GB300 runs FP64 at a small
+                          fraction of its FP32 rate); their squared norms
+                          are summed in FP32.              (default 1e-7)  */
   int32_t block_size;  /* threads per block of the iteration kernel (multiple of
                           32, <= 512); 0 = 512 with two lanes per node or when
                           the mesh has more nodes than 256 per SM, else 256 */
@@ -151,7 +152,7 @@ typedef struct {
   int32_t smooth_passes; /* explicit mode: Eq. 14 passes per iteration (the
                           paper applies one and notes that more give a
                           smoother field); 0 = 1, at most 64; other modes
-                          and the cluster engine accept only 1.             */
+                          accept only 1.                                    */
   int32_t host_topology; /* 0: the mesh pre-computation of Algorithm 1
                           (incidence and 1-ring CSRs, edges, quadrature
                           weights, operators) runs on the device; 1: on the
@@ -189,14 +190,14 @@ typedef struct {
   int32_t last_pcg_iters;      /* CG iterations of the last solve (S1/S2)    */
   int32_t max_pcg_iters;       /* largest count since create / reset         */
   int32_t not_converged;       /* solves that stopped at the cap             */
-  double last_rel_resid;       /* ||b - A u'|| / ||b|| (FP64) of the last
-                                  solve, max over x and y                    */
+  double last_rel_resid;       /* ||b - A u'|| / ||b|| of the last solve, max
+                                  over x and y (residual in float-float,
+                                  norms in FP32, see pcg_rtol)               */
   double last_energy;          /* data energy at the last sampled iterate    */
-  int32_t grid_blocks;         /* launch shape of the iteration kernel (CTAs
-                                  of the cluster for the cluster engine)      */
+  int32_t grid_blocks;         /* launch shape of the iteration kernel        */
   int32_t block_size;
   int32_t device_status;       /* raw device status bits (0 = clean)         */
-  int32_t engine;              /* MREG_ENGINE_GRID or MREG_ENGINE_CLUSTER     */
+  int32_t engine;              /* MREG_ENGINE_GRID                            */
   int32_t node_lanes;          /* lanes per node of the iteration kernel      */
 } mreg_stats_t;
 
@@ -215,8 +216,9 @@ enum {
                                 last mreg_step call                           */
   MREG_FIELD_PCG_ITERS = 8,  /* n int32: CG iterations of each iteration of
                                 the last mreg_step call                       */
-  MREG_FIELD_PCG_RESID = 9,  /* n double: final relative FP64 residual of each
-                                solve of the last mreg_step call              */
+  MREG_FIELD_PCG_RESID = 9,  /* n double: final relative residual of each
+                                solve of the last mreg_step call (as
+                                mreg_stats_t.last_rel_resid)                  */
   MREG_FIELD_COEF_TE_BF16 = 10 /* H x W uint16: the BF16 copy of Te's
                                 coefficients (bit patterns); 0 elements when
                                 coeff_bf16 is off                             */
@@ -297,8 +299,9 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
 mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
                              double* energy_dev, float* grad_dev, void* stream);
 
-/* MSD of the current displacement (abstract; Table 1), FP64.  Blocks until
- * the value is on the host.                                                 */
+/* MSD of the current displacement (abstract; Table 1): FP32 squared
+ * differences summed in float-float, the mean taken and returned in FP64.
+ * Blocks until the value is on the host.                                    */
 mreg_status mreg_msd(mreg_handle* h, double* out_host, void* stream);
 
 /* Energy of Eq. 1 at the current u: E = D + alpha S, FP64.  D is the data
@@ -326,7 +329,8 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
                            int64_t* count_out, void* stream);
 
 /* Wait for the stream and report the solver / device state.  Returns
- * MREG_ERR_DEVICE_CHECK if a bounded device wait gave up, else
+ * MREG_ERR_DEVICE_CHECK if a bounded device wait gave up (the handle's later
+ * steps then return MREG_ERR_DEVICE_CHECK until mreg_reset), else
  * MREG_ERR_NOT_CONVERGED if a solve hit its cap since the last reset, else
  * MREG_OK.  out may be NULL.                                                */
 mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream);
@@ -335,31 +339,53 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream);
  * NULL is accepted.                                                         */
 void mreg_destroy(mreg_handle* h);
 
+/* Test of the failure path of the bounded device waits (the paper has no
+ * counterpart).  Every grid-barrier wait of the iteration kernel is bounded;
+ * this call arms the next iteration-kernel launch of h (the next mreg_step,
+ * or the forward run of mreg_unroll_grad) so that block `block` of its grid
+ * leaves out its arrival at grid barrier number `barrier` (1 = the first
+ * barrier of the launch) and every barrier wait of that launch gives up
+ * after timeout_ns.  The waits then run out: the launch ends early, with the
+ * device status that mreg_stats reports as MREG_ERR_DEVICE_CHECK, and the
+ * GPU context stays usable.  A launch whose barrier number `barrier` is
+ * never reached runs normally.  After a wait has given up, later launches
+ * of the handle leave at once, and once mreg_stats has reported the failure
+ * mreg_step and mreg_unroll_grad return MREG_ERR_DEVICE_CHECK; mreg_reset
+ * clears the state.
+ *   block       0 <= block < mreg_stats_t.grid_blocks
+ *   barrier     >= 1
+ *   timeout_ns  in [1e5, 2e9]
+ * Errors: INVALID_ARG for values out of range.  Host-only (enqueues nothing). */
+mreg_status mreg_test_barrier_timeout(mreg_handle* h, int32_t block, int32_t barrier,
+                                      int64_t timeout_ns);
+
 /* Largest image (width * height) that mreg_prefilter_noalloc accepts. */
 #define MREG_NOALLOC_MAX_PIXELS (1024 * 1024)
 
 /* B-spline coefficients of one image without allocating device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc, such as code running while a stream is captured
- * into a CUDA graph, hosts whose memory pool owns all device memory, and
- * loops that must not pay for a device-synchronising allocation.  It runs
- * the same prefilter as mreg_create (step a0) on a caller's image and writes
- * the coefficients to the caller's buffer; its only scratch is a fixed
- * 4 MiB array inside the library (MREG_NOALLOC_MAX_PIXELS floats), which
- * every GPU that loads the library holds until the process exits.
- *   img_dev    device image, width x height float32, row stride row_stride
- *              (elements, >= width)
- *   coef_dev   device output, width x height float32, row stride width;
- *              must not overlap img_dev
+ * cannot call cudaMalloc, such as hosts whose memory pool owns all device
+ * memory and forbids allocations behind its back, and latency-bound loops
+ * that must not pay for cudaMalloc / cudaFree (both synchronise the device).
+ * It runs the same prefilter as mreg_create (step a0) on a caller's image
+ * and writes the coefficients to the caller's buffer; its only scratch is a
+ * fixed 4 MiB array inside the library (MREG_NOALLOC_MAX_PIXELS floats),
+ * which every GPU that loads the library holds until the process exits.
+ *   img_dev    device image of the current device, width x height float32,
+ *              row stride row_stride (elements, >= width)
+ *   coef_dev   device output of the current device, width x height float32,
+ *              row stride width; must not overlap img_dev
  *   stream     cudaStream_t as void*; the call is asynchronous
  * Errors: INVALID_ARG for NULL pointers, images smaller than 2x2, a row
- * stride below the width, or width * height > MREG_NOALLOC_MAX_PIXELS; CUDA
- * if a launch fails.  The first call on a device looks up the scratch array's
- * device address (cudaGetSymbolAddress) for that device, so make that first
- * call before any stream capture.  All calls share the one scratch array:
- * calls that may overlap on the GPU (different streams, or several host
- * threads) race on it and must be serialised by the caller.              */
+ * stride below the width, width * height > MREG_NOALLOC_MAX_PIXELS, or an
+ * image or output that is not device memory of the current device (host
+ * memory, another GPU's memory); CUDA if a launch fails.  The first call on
+ * a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) for that device, so make that first call before
+ * any stream capture.  All calls share the one scratch array: calls that may
+ * overlap on the GPU (different streams, or several host threads) race on
+ * it and must be serialised by the caller.                                 */
 mreg_status mreg_prefilter_noalloc(const float* img_dev, int64_t row_stride, float* coef_dev,
                                    int32_t width, int32_t height, void* stream);
 

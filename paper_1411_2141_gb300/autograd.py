@@ -57,6 +57,7 @@ class UnrolledWarpEnergy(torch.autograd.Function):
         grad = torch.empty_like(uc) if ctx.needs_input_grad[0] else None
         reg.unroll_grad(uc, n_iters, energy, grad)
         ctx.save_for_backward(grad)
+        ctx.reg = reg
         return energy.reshape(())
 
     @staticmethod
@@ -64,6 +65,10 @@ class UnrolledWarpEnergy(torch.autograd.Function):
         (grad,) = ctx.saved_tensors
         if grad is None:
             return None, None, None
+        # the forward run is a persistent kernel with bounded grid-barrier
+        # waits: raise (MregError, MREG_ERR_DEVICE_CHECK) if one gave up
+        # rather than hand back a gradient of an unfinished run
+        ctx.reg.stats()
         return (grad * g_energy.to(grad.dtype)), None, None
 
 

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libmreg.so")
 
-SOURCES = ["api.cpp", "batch_api.cpp", "prefilter.cu", "iterate.cu", "iterate_cluster.cu",
+SOURCES = ["api.cpp", "batch_api.cpp", "prefilter.cu", "iterate.cu",
            "batch.cu", "warp.cu", "topology.cu", "prefilter_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

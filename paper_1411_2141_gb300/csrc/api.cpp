@@ -267,9 +267,13 @@ struct mreg_handle {
   int grid = 0, block = 0, warp_grid = 0;
   int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
   int lanes = 1;  // lanes per node of the iteration kernel
-  int engine = MREG_ENGINE_GRID, cl_size = 0, cl_chunk = 0;
+  int engine = MREG_ENGINE_GRID;
   float area_floor = 0.0f;
   int iterations_done = 0, last_n_iters = 0, last_force_buf = 0;
+  // failure-path test (mreg_test_barrier_timeout): armed for the next launch
+  int stall_block = -1, stall_barrier = 0;
+  uint64_t stall_timeout_ns = 0;
+  bool device_failed = false;   // a barrier wait gave up; cleared by reset
   void* arena = nullptr;
   // device arrays
   float *Re = nullptr, *Te = nullptr, *cRe = nullptr, *cTe = nullptr, *tmp = nullptr;
@@ -310,8 +314,6 @@ struct mreg_handle {
   mreg::IterArgs iter_args(int n_iters, int it0) const {
     mreg::IterArgs a{};
     a.it0 = it0;
-    a.chunk = cl_chunk;
-    a.inv_chunk = cl_chunk > 0 ? 1.0f / (float)cl_chunk : 0.0f;
     a.nV = nV;
     a.nE = nE;
     a.W = W;
@@ -357,6 +359,9 @@ struct mreg_handle {
     a.part = part;
     a.bar = bar;
     a.status = status;
+    a.barrier_timeout_ns = stall_barrier > 0 ? stall_timeout_ns : mreg::kBarrierTimeoutNs;
+    a.stall_block = stall_block;
+    a.stall_barrier = stall_barrier;
     a.energy_hist = energy_hist;
     a.epart = epart;
     a.ewarps = (grid * block + 31) / 32;
@@ -406,7 +411,8 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 512 || o.block_size % 32))
     return fail(MREG_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
   if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
-  if (o.engine < 0 || o.engine > 2) return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
+  if (o.engine != MREG_ENGINE_AUTO && o.engine != MREG_ENGINE_GRID)
+    return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
     return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
   if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
@@ -419,10 +425,9 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
     return fail(MREG_ERR_INVALID_ARG, "smooth_passes > 1 needs the explicit mode");
   if (o.node_lanes < 0 || o.node_lanes > 2)
     return fail(MREG_ERR_INVALID_ARG, "node_lanes must be 0, 1 or 2");
-  if (o.node_lanes == 2 && (o.mode == MREG_MODE_EXPLICIT || o.team_blocks_per_sm == 2 ||
-                            o.engine == MREG_ENGINE_CLUSTER))
+  if (o.node_lanes == 2 && (o.mode == MREG_MODE_EXPLICIT || o.team_blocks_per_sm == 2))
     return fail(MREG_ERR_INVALID_ARG,
-                "node_lanes 2 needs an implicit mode on the grid engine with team_blocks_per_sm 1");
+                "node_lanes 2 needs an implicit mode with team_blocks_per_sm 1");
   const double l = o.lambda < 0.0 ? tau * alpha : o.lambda;
   if (!std::isfinite(l)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
   *lam = l;
@@ -479,6 +484,9 @@ mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
   h->iterations_done = 0;
   h->last_n_iters = 0;
   h->last_force_buf = 0;
+  h->device_failed = false;
+  h->stall_block = -1;
+  h->stall_barrier = 0;
   if (check_cover) {
     int unc = 0;
     CK(cudaMemcpyAsync(&unc, h->counters, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
@@ -595,39 +603,6 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
     return fail(MREG_ERR_INVALID_ARG, "grid_blocks %d exceeds the %d co-resident blocks", h->grid,
                 max_grid);
   h->warp_grid = mreg::warp_grid_blocks(W, H, h->num_sms);
-
-  // cluster engine: the whole iteration state in one cluster's shared memory
-  // AUTO runs the grid engine: on the 512^2 / 20k-node pair it measured 41 us per
-  // iteration against 74 us for the cluster engine (16 SMs are ALU-bound there).
-  if (o.engine == MREG_ENGINE_CLUSTER && o.smooth_passes > 1)
-    return fail(MREG_ERR_INVALID_ARG, "the cluster engine runs one smoothing pass per iteration");
-  if (o.engine == MREG_ENGINE_CLUSTER && h->form != mreg::kFormFemEdges) {
-    int smem_optin = 0;
-    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev),
-       "attribute");
-    // about 512 nodes per CTA (one per thread), at most 16 CTAs
-    for (int C0 = std::min(16, std::max(1, (h->nV + 511) / 512)); C0 <= 16 && !h->cl_size; ++C0) {
-      const int chunk = (h->nV + C0 - 1) / C0;
-      const int C = (h->nV + chunk - 1) / chunk;
-      const size_t smem = mreg::cluster_smem_bytes(h->form, chunk) + 4096;
-      if (smem > (size_t)smem_optin) continue;
-      int active = 0;
-      if (mreg::cluster_prepare(h->form, h->grad, C, chunk, &active) != cudaSuccess) {
-        cudaGetLastError();   // clear the (non-sticky) error of an unsupported shape
-        continue;
-      }
-      if (active >= 1) {
-        h->cl_size = C;
-        h->cl_chunk = chunk;
-      }
-    }
-    if (!h->cl_size)
-      return fail(MREG_ERR_INVALID_ARG, "the cluster engine cannot hold %d nodes in one cluster",
-                  h->nV);
-    h->engine = MREG_ENGINE_CLUSTER;
-  } else if (o.engine == MREG_ENGINE_CLUSTER) {
-    return fail(MREG_ERR_INVALID_ARG, "the cluster engine does not run the edge-midpoint form");
-  }
 
   // one arena for every device array
   // the device build writes into arrays sized for its capacities
@@ -786,6 +761,8 @@ mreg_status mreg_reset(mreg_handle* h, void* stream) {
 mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
   if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
   if (n_iters < 0) return fail(MREG_ERR_INVALID_ARG, "n_iters must be >= 0");
+  if (h->device_failed)
+    return fail(MREG_ERR_DEVICE_CHECK, "an earlier launch gave up at a grid barrier; reset first");
   if (n_iters == 0) return MREG_OK;
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   // Long runs are split into launches of at most kChunk iterations, which
@@ -793,14 +770,11 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
   for (int it0 = 0; it0 < n_iters; it0 += kChunk) {
     const int n = std::min(kChunk, n_iters - it0);
     const mreg::IterArgs a = h->iter_args(n, it0);
-    if (h->engine == MREG_ENGINE_CLUSTER) {
-      CK(mreg::launch_cluster(h->form, h->grad, a, h->cl_size, (cudaStream_t)stream),
-         "cluster iteration kernel launch");
-    } else {
-      CK(mreg::launch_iterate(h->form, h->grad, h->minb, h->lanes, a, h->grid, h->block,
-                              (cudaStream_t)stream),
-         "iteration kernel launch");
-    }
+    h->stall_block = -1;   // an armed stall applies to one launch only
+    h->stall_barrier = 0;
+    CK(mreg::launch_iterate(h->form, h->grad, h->minb, h->lanes, a, h->grid, h->block,
+                            (cudaStream_t)stream),
+       "iteration kernel launch");
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
   }
   h->iterations_done += n_iters;
@@ -845,6 +819,8 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
     return fail(MREG_ERR_INVALID_ARG,
                 "the unrolled gradient needs the explicit mode with the spline gradient");
   if (n_iters < 0 || n_iters > 100000) return fail(MREG_ERR_INVALID_ARG, "n_iters out of range");
+  if (h->device_failed)
+    return fail(MREG_ERR_DEVICE_CHECK, "an earlier launch gave up at a grid barrier; reset first");
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   // states u_0 .. u_{K-1} densely (K x nV float2), then three vectors
@@ -865,19 +841,10 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   float2* va = (float2*)(base + states);
   float2* vb = (float2*)(base + states + vec);
   float2* vc = (float2*)(base + states + 2 * vec);
-  // forward: u_0 .. u_{K-1} kept.  The grid engine's iteration kernel stores
-  // each iteration's starting state itself (one launch per 1024 iterations);
-  // the cluster engine runs one step per launch after a copy of the state.
+  // forward: u_0 .. u_{K-1} kept.  The iteration kernel stores each
+  // iteration's starting state itself (one launch per 1024 iterations).
   CK(cudaMemcpyAsync(h->u, u0_dev, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s), "copy u0");
-  if (h->engine == MREG_ENGINE_CLUSTER) {
-    for (int k = 0; k < n_iters; ++k) {
-      CK(cudaMemcpyAsync(ustates + (size_t)k * h->nV, h->u, sizeof(float2) * h->nV,
-                         cudaMemcpyDeviceToDevice, s),
-         "copy state");
-      mreg_status st = mreg_step(h, 1, stream);
-      if (st) return st;
-    }
-  } else if (n_iters > 0) {
+  if (n_iters > 0) {
     h->u_keep = ustates;
     const mreg_status st = mreg_step(h, n_iters, stream);
     h->u_keep = nullptr;
@@ -1047,17 +1014,34 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
     out->last_pcg_iters = (int32_t)last[2];
     out->max_pcg_iters = (int32_t)last[3];
     out->not_converged = (int32_t)last[4];
-    out->grid_blocks = h->engine == MREG_ENGINE_CLUSTER ? h->cl_size : h->grid;
-    out->block_size = h->engine == MREG_ENGINE_CLUSTER ? mreg::cluster_block_size() : h->block;
+    out->grid_blocks = h->grid;
+    out->block_size = h->block;
     out->device_status = status;
     out->engine = h->engine;
-    out->node_lanes = h->engine == MREG_ENGINE_CLUSTER ? 1 : h->lanes;
+    out->node_lanes = h->lanes;
   }
-  if (status & mreg::kStatusBarrierTimeout)
+  if (status & mreg::kStatusBarrierTimeout) {
+    h->device_failed = true;
     return fail(MREG_ERR_DEVICE_CHECK, "a grid barrier of the iteration kernel timed out");
+  }
   if (status & mreg::kStatusNotConverged)
     return fail(MREG_ERR_NOT_CONVERGED, "%d solves stopped at the CG iteration cap (%d)",
                 (int)last[4], h->opts.pcg_maxit);
+  return MREG_OK;
+}
+
+mreg_status mreg_test_barrier_timeout(mreg_handle* h, int32_t block, int32_t barrier,
+                                      int64_t timeout_ns) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  if (block < 0 || block >= h->grid)
+    return fail(MREG_ERR_INVALID_ARG, "block %d is not in the iteration grid of %d blocks", block,
+                h->grid);
+  if (barrier < 1) return fail(MREG_ERR_INVALID_ARG, "barrier numbers start at 1");
+  if (timeout_ns < 100000 || timeout_ns > (int64_t)mreg::kBarrierTimeoutNs)
+    return fail(MREG_ERR_INVALID_ARG, "timeout_ns must be in [1e5, 2e9]");
+  h->stall_block = block;
+  h->stall_barrier = barrier;
+  h->stall_timeout_ns = (uint64_t)timeout_ns;
   return MREG_OK;
 }
 

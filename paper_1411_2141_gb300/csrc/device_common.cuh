@@ -191,16 +191,20 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Barrier over all blocks of a cooperative launch.  The counter starts at 0
 // at launch; barrier number e completes when it reaches e * nblocks.  Every
-// wait is bounded (kBarrierTimeoutNs): on timeout the block raises
-// kStatusBarrierTimeout | kStatusAbort and every block leaves at its next
-// barrier.  Must be reached by all threads of all blocks.
-constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s
-
+// wait is bounded (timeout_ns, kBarrierTimeoutNs = 2 s by default): on timeout the
+// block raises kStatusBarrierTimeout | kStatusAbort and every block leaves at
+// its next barrier.  Must be reached by all threads of all blocks.
+//
+// skip_epoch > 0 makes this block leave out its arrival at barrier number
+// skip_epoch (a test of the failure path: the other blocks' waits, and its
+// own, then run out and the launch ends with the status above).
 struct GridBarrier {
   unsigned long long* counter;
   int* status;
   unsigned long long nblocks;
   unsigned long long epoch;
+  uint64_t timeout_ns;
+  unsigned long long skip_epoch;
 
   // Returns false (block-uniformly) when the kernel must stop.  The wait is a
   // bare acquire-load loop; the abort flag and the clock are looked at only
@@ -209,7 +213,7 @@ struct GridBarrier {
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
-      red_release_add(counter, 1ull);
+      if (epoch != skip_epoch) red_release_add(counter, 1ull);
       const unsigned long long target = epoch * nblocks;
       int flag = 0;
       if (ld_acquire_u64(counter) < target) {
@@ -221,7 +225,7 @@ struct GridBarrier {
               flag = 1;
               break;
             }
-            if (global_ns() - t0 > kBarrierTimeoutNs) {
+            if (global_ns() - t0 > timeout_ns) {
               atomicOr(status, kStatusBarrierTimeout | kStatusAbort);
               flag = 1;
               break;

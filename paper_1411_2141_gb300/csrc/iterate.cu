@@ -18,6 +18,18 @@ struct GridTeam {
   __device__ __forceinline__ bool sync() { return gb.sync(s_flag); }
 };
 
+__device__ __forceinline__ GridBarrier grid_barrier(const IterArgs& a) {
+  return GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull, a.barrier_timeout_ns,
+                     (int)blockIdx.x == a.stall_block ? (unsigned long long)a.stall_barrier : 0ull};
+}
+
+// A handle whose earlier launch gave up at a barrier keeps the abort bit
+// until it is reset; its later launches leave at once (every block reads the
+// same bit: nothing in this launch sets it before a barrier wait times out).
+__device__ __forceinline__ bool aborted(const IterArgs& a) {
+  return (ld_volatile_i32(a.status) & kStatusAbort) != 0;
+}
+
 // MINB: blocks per SM the register budget is sized for (1: up to 128
 // registers per thread; 2: up to 64 for 512-thread blocks, the rest in local
 // memory), picked by the host from the mesh size.
@@ -25,8 +37,8 @@ template <int GRAD, int MINB>
 __global__ void __launch_bounds__(kIterBlockMax, MINB) k_explicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
-  GridTeam team{GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull}, &s_flag,
-                (int)blockIdx.x, (int)gridDim.x};
+  if (aborted(a)) return;
+  GridTeam team{grid_barrier(a), &s_flag, (int)blockIdx.x, (int)gridDim.x};
   run_explicit<GRAD>(a, team, dsm);
 }
 
@@ -35,8 +47,8 @@ template <int FORM, int GRAD, int MINB, int L>
 __global__ void __launch_bounds__(kIterBlockMax, MINB) k_implicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
-  GridTeam team{GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull}, &s_flag,
-                (int)blockIdx.x, (int)gridDim.x};
+  if (aborted(a)) return;
+  GridTeam team{grid_barrier(a), &s_flag, (int)blockIdx.x, (int)gridDim.x};
   run_implicit<FORM, GRAD, L>(a, team, dsm);
 }
 

@@ -13,6 +13,9 @@ constexpr int kStatusNotConverged = 1;   // a CG solve stopped at its cap
 constexpr int kStatusBarrierTimeout = 2; // a grid barrier wait gave up
 constexpr int kStatusAbort = 4;          // every block must leave the kernel
 
+// Default bound of every grid-barrier wait of the persistent kernels.
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s
+
 // Floats in one block's reduction record (partial sums carried through one
 // grid barrier), and the largest number of warps per block.
 constexpr int kRec = 12;
@@ -30,8 +33,6 @@ enum Form : int {
 struct IterArgs {
   int nV, nE, W, H, n_iters, it0, maxit, hist_cap;   // it0: history index of iteration 0
   int smooth_passes;     // S0: Eq. 14 passes per iteration (>= 1)
-  int chunk;             // cluster engine: nodes per CTA
-  float inv_chunk;       // 1 / chunk
   float tau, lam, area_floor, rtol2;
   float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
   // read-only mesh / operator data
@@ -70,6 +71,9 @@ struct IterArgs {
   float* part;           // 2 * grid * kRec partial sums (two halves, alternating)
   unsigned long long* bar;  // barrier counter (zeroed before each launch)
   int* status;           // device status bits
+  uint64_t barrier_timeout_ns;   // bound of every grid-barrier wait
+  int stall_block;       // failure-path test: this block skips its arrival at
+  int stall_barrier;     // grid barrier number stall_barrier (0 = never)
   double* energy_hist;   // per-iteration data energy (hist_cap entries)
   float2* epart;         // grid engine: per-warp energy partials, (n_iters + 1) x ewarps
   int ewarps;            // warps of the grid-engine launch
@@ -156,12 +160,6 @@ cudaError_t launch_unroll_adjoint(const UnrollArgs& a, const float2* ustates, in
 cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tpart,
                              const int* inc_ptr, const int* inc_tri, int nV, double* energy_out,
                              float2* grad_out, cudaStream_t s);
-
-// Cluster engine (whole iteration state in the shared memory of one cluster).
-size_t cluster_smem_bytes(int form, int chunk);
-int cluster_block_size();
-cudaError_t cluster_prepare(int form, int grad, int C, int chunk, int* max_active);
-cudaError_t launch_cluster(int form, int grad, const IterArgs& a, int C, cudaStream_t s);
 
 // Iteration kernel: occupancy query and cooperative launch.
 // The data term and the regulariser of Eq. 1 at a.u into out[0], out[1]

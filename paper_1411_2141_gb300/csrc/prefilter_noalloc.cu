@@ -1,14 +1,14 @@
 // mreg_prefilter_noalloc: the cubic B-spline prefilter of one image for
 // callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (cudaMalloc is not a stream operation and would
-// break the capture), hosts that hand every byte of device memory to their
-// own pool and forbid other allocations, and latency-bound loops that must
-// not pay for cudaMalloc/cudaFree, which synchronise the device.  For them
-// this entry point runs the same two prefilter kernels as the library's
-// set-up, but takes the intermediate image (the result of the row pass) from
-// a fixed scratch array that is part of the library itself.
+// Some callers cannot call cudaMalloc: hosts that hand every byte of device
+// memory to their own pool (a framework's caching allocator, an embedding
+// runtime with a fixed memory budget) and forbid allocations behind the
+// pool's back, and latency-bound loops that must not pay for
+// cudaMalloc/cudaFree, which synchronise the device.  For them this entry
+// point runs the same two prefilter kernels as the library's set-up, but
+// takes the intermediate image (the result of the row pass) from a fixed
+// scratch array that is part of the library itself.
 //
 // The scratch is a file-scope __device__ array of kNoAllocMaxPixels floats
 // (4 MiB).  Every GPU that loads the library holds it until the process
@@ -38,6 +38,25 @@ namespace mreg {
 mreg_status set_error(mreg_status st, const char* msg);
 }  // namespace mreg
 
+namespace {
+
+// The kernels may only be given memory that the current device can use as
+// its own: device (or managed) memory of device dev.  A host pointer, or
+// memory of another GPU, is rejected before anything is launched.
+mreg_status check_device_pointer(const void* p, int dev, const char* what) {
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();   // the query's error is not sticky; clear it
+    return mreg::set_error(MREG_ERR_INVALID_ARG, what);
+  }
+  if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+    return mreg::set_error(MREG_ERR_INVALID_ARG, what);
+  return MREG_OK;
+}
+
+}  // namespace
+
 extern "C" mreg_status mreg_prefilter_noalloc(const float* img_dev, int64_t row_stride,
                                               float* coef_dev, int32_t width, int32_t height,
                                               void* stream) {
@@ -57,6 +76,12 @@ extern "C" mreg_status mreg_prefilter_noalloc(const float* img_dev, int64_t row_
   if (e != cudaSuccess) return mreg::set_error(MREG_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices)
     return mreg::set_error(MREG_ERR_INVALID_ARG, "mreg_prefilter_noalloc: device index too large");
+  mreg_status st = check_device_pointer(
+      img_dev, dev, "mreg_prefilter_noalloc: the image is not device memory of the current device");
+  if (st != MREG_OK) return st;
+  st = check_device_pointer(
+      coef_dev, dev, "mreg_prefilter_noalloc: the output is not device memory of the current device");
+  if (st != MREG_OK) return st;
   float* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mutex);

@@ -396,7 +396,8 @@ __global__ void __launch_bounds__(kUnrollBlock) k_unroll_adjoint(
     const UnrollArgs a, const float2* __restrict__ ustates, int n_iters, int passes, float2* va,
     float2* vb, float2* vc, unsigned long long* bar, int* status) {
   __shared__ int s_flag;
-  GridBarrier gb{bar, status, (unsigned long long)gridDim.x, 0ull};
+  GridBarrier gb{bar, status, (unsigned long long)gridDim.x, 0ull, kBarrierTimeoutNs, 0ull};
+  if (ld_volatile_i32(status) & kStatusAbort) return;   // an earlier launch gave up
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (int k = n_iters - 1; k >= 0; --k) {
     for (int p = 1; p < passes; ++p) {

@@ -58,8 +58,7 @@ GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
 QUADS = {"Q0": MREG_QUAD_NODES, "Q1": MREG_QUAD_EDGE_MIDPOINTS}
 MREG_ENGINE_AUTO = 0
 MREG_ENGINE_GRID = 1
-MREG_ENGINE_CLUSTER = 2
-ENGINES = {"auto": MREG_ENGINE_AUTO, "grid": MREG_ENGINE_GRID, "cluster": MREG_ENGINE_CLUSTER}
+ENGINES = {"auto": MREG_ENGINE_AUTO, "grid": MREG_ENGINE_GRID}
 
 
 class mreg_mesh(C.Structure):
@@ -100,6 +99,7 @@ EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mr
            "mreg_msd", "mreg_energy", "mreg_energy_terms", "mreg_get_u", "mreg_set_u", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
            "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
+           "mreg_test_barrier_timeout",
            "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
            "mreg_batch_shape", "mreg_batch_iterate_ms", "mreg_batch_msd", "mreg_batch_get_field",
            "mreg_batch_stats", "mreg_batch_destroy"]
@@ -146,6 +146,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_prefilter_noalloc": ([vp, i64, vp, i32, i32, vp], i32),
         "mreg_warp_energy_grad": ([vp, vp, vp, vp, vp], i32),
         "mreg_unroll_grad": ([vp, vp, i32, vp, vp, vp], i32),
+        "mreg_test_barrier_timeout": ([vp, i32, i32, i64], i32),
         "mreg_batch_create": ([i32, C.POINTER(mreg_mesh), C.POINTER(mreg_image),
                                C.POINTER(mreg_image), dbl, dbl, C.POINTER(mreg_options), vp,
                                C.POINTER(vp)], i32),
@@ -192,9 +193,15 @@ def _is_torch_cuda(x) -> bool:
 
 
 def prefilter_noalloc(img, out, stream=None):
-    """B-spline coefficients of a device image (2-D float32 torch tensor with
-    unit column stride) into ``out`` (contiguous, same shape) without any
-    device allocation; asynchronous on ``stream``."""
+    """B-spline coefficients of a device image (2-D float32 CUDA tensor on the
+    current device, unit column stride) into ``out`` (contiguous, same shape
+    and device) without any device allocation; asynchronous on ``stream``."""
+    if not (_is_torch_cuda(img) and _is_torch_cuda(out)):
+        raise ValueError("img and out must be CUDA tensors")
+    import torch
+    dev = torch.cuda.current_device()
+    if img.device.index != dev or out.device.index != dev:
+        raise ValueError("img and out must be on the current CUDA device")
     if str(img.dtype) != "torch.float32" or img.dim() != 2 or img.stride(1) != 1:
         raise ValueError("img must be a 2-D float32 tensor with unit column stride")
     if tuple(out.shape) != tuple(img.shape) or not out.is_contiguous():
@@ -340,6 +347,12 @@ class Registration:
 
     def step(self, n_iters: int, stream=None):
         _check(load().mreg_step(self._h, int(n_iters), _stream_ptr(stream)), "mreg_step")
+
+    def test_barrier_timeout(self, block: int, barrier: int, timeout_ns: int):
+        """Arm the next iteration launch to run out of one grid-barrier wait
+        (a test of the failure path; see mreg_test_barrier_timeout)."""
+        _check(load().mreg_test_barrier_timeout(self._h, int(block), int(barrier),
+                                                int(timeout_ns)), "mreg_test_barrier_timeout")
 
     def warp(self, out=None, msd_out=None, stream=None):
         """Asynchronous warp into device tensors ``out`` (H x W float32) and

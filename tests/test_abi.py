@@ -145,8 +145,7 @@ def test_option_validation_of_the_newer_fields(lib):
     _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S0", node_lanes=2))
     _expect(E.MREG_ERR_INVALID_ARG,
             lambda: _create(V, T, img, img, mode="S1", node_lanes=2, team_blocks_per_sm=2))
-    _expect(E.MREG_ERR_INVALID_ARG,
-            lambda: _create(V, T, img, img, mode="S1", node_lanes=2, engine="cluster"))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, engine=2))
     _expect(E.MREG_ERR_INVALID_ARG, lambda: mreg.Batch([(V, T, img, img)], 0.1, 1.0, mode="S1",
                                                        node_lanes=2))
     o = mreg.make_options(host_topology=True)

@@ -93,10 +93,11 @@ def test_bf16_registration_config0(mreg, c0, mode, grad):
 
 
 def test_config2_full_size(mreg, c2):
-    """The 2048^2 / 250k-node pair: FP32 form to the FP32 bar, BF16 form to
-    its stated bound, both against the same FP64 oracle trajectory (20 of the
-    300 iterations, to keep the oracle in seconds)."""
-    n = 20
+    """The 2048^2 / 250k-node pair over its full 300 iterations: FP32 form to
+    the FP32 bar, BF16 form to its stated bound, both against the same FP64
+    oracle trajectory (a few minutes of the oracle on one host core)."""
+    n = c2.spec.n_iter
+    assert n == 300
     pb = _oracle(c2)
     u_ref, e_ref = pb.run(n)
     msd_ref = pb.msd(u_ref)

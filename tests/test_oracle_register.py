@@ -248,3 +248,65 @@ def test_total_energy_decreases_for_the_umbrella_form(small):
         e = pb.total_energy(u)
         assert e < e_prev
         e_prev = e
+
+
+def _exact_orient(ax, ay, bx, by, px, py):
+    """Orientation of p against a -> b in exact rational arithmetic (every
+    float is a dyadic rational, so Fraction holds it exactly)."""
+    from fractions import Fraction as Fr
+    ax, ay, bx, by, px, py = (Fr(float(v)) for v in (ax, ay, bx, by, px, py))
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax)
+
+
+def test_point_location_exact_on_an_integer_mesh():
+    """An independent pin of the owner rule (smallest index among the closed
+    triangles that contain the pixel centre): a Delaunay mesh whose nodes all
+    sit on pixel centres, so that many pixel centres lie exactly on edges and
+    at vertices, located by exact integer orientation tests and compared with
+    locate_pixels."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(5)
+    W, H = 23, 17
+    border = [(x, 0) for x in range(0, W, 4)] + [(x, H - 1) for x in range(0, W, 4)] \
+        + [(0, y) for y in range(0, H, 4)] + [(W - 1, y) for y in range(0, H, 4)] \
+        + [(W - 1, H - 1)]
+    inner = {(int(x), int(y)) for x, y in zip(rng.integers(1, W - 1, 40), rng.integers(1, H - 1, 40))}
+    P = np.array(sorted(set(border) | inner), dtype=np.int64)
+    T = Delaunay(P.astype(float)).simplices.astype(np.int64)
+    A2 = ((P[T[:, 1], 0] - P[T[:, 0], 0]) * (P[T[:, 2], 1] - P[T[:, 0], 1])
+          - (P[T[:, 1], 1] - P[T[:, 0], 1]) * (P[T[:, 2], 0] - P[T[:, 0], 0]))
+    T[A2 < 0] = T[A2 < 0][:, [0, 2, 1]]   # counter-clockwise
+    T = T[A2 != 0]
+    owner = register.locate_pixels(P.astype(np.float64), T, W, H)
+    on_edge = 0
+    for y in range(H):
+        for x in range(W):
+            best = -1
+            for t, (a, b, c) in enumerate(T):
+                o = [(P[j, 0] - P[i, 0]) * (y - P[i, 1]) - (P[j, 1] - P[i, 1]) * (x - P[i, 0])
+                     for i, j in ((a, b), (b, c), (c, a))]   # exact in int64
+                if min(o) >= 0:
+                    on_edge += min(o) == 0
+                    best = t
+                    break
+            assert owner[y, x] == best, (x, y)
+    assert on_edge > 50   # the tie rule was really exercised
+
+
+def test_point_location_owner_contains_the_pixel_exactly(small):
+    """On a generated mesh (float coordinates), the owner of every pixel
+    contains the pixel centre in exact rational arithmetic: its three exact
+    orientations (the barycentric coordinates times twice its area) are >= 0
+    and sum to twice its area."""
+    P = small.V.astype(np.float64)
+    T = small.T.astype(np.int64)
+    H, W = small.Re.shape
+    owner = register.locate_pixels(P, T, W, H)
+    for y in range(0, H, 2):
+        for x in range(0, W, 2):
+            a, b, c = T[owner[y, x]]
+            o = [_exact_orient(P[i, 0], P[i, 1], P[j, 0], P[j, 1], x, y)
+                 for i, j in ((b, c), (c, a), (a, b))]
+            area2 = _exact_orient(P[a, 0], P[a, 1], P[b, 0], P[b, 1], P[c, 0], P[c, 1])
+            assert min(o) >= 0, (x, y)
+            assert sum(o) == area2

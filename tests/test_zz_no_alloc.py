@@ -1,7 +1,8 @@
 """The allocation-free prefilter entry point (mreg_prefilter_noalloc).
 
-It serves callers that cannot call cudaMalloc (stream capture, externally
-owned memory pools).  It must give the same B-spline coefficients as the
+It serves callers that cannot call cudaMalloc (hosts whose own memory pool
+owns all device memory, loops that must not pay for a device-synchronising
+allocation).  It must give the same B-spline coefficients as the
 regular set-up path (mreg_create, read back with mreg_get_field), on two calls
 in a row that share its fixed scratch array.  This file is named so that
 pytest collects it last.
@@ -67,3 +68,26 @@ def test_noalloc_prefilter_rejects_oversized_images(mreg):
         mreg.prefilter_noalloc(img, out)
     assert e.value.status == mreg.MREG_ERR_INVALID_ARG
     assert "MREG_NOALLOC_MAX_PIXELS" in str(e.value)
+
+
+def test_noalloc_prefilter_rejects_memory_the_gpu_cannot_use(mreg):
+    H, W = 64, 48
+    out = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):   # the binding refuses CPU tensors
+        mreg.prefilter_noalloc(torch.zeros((H, W), dtype=torch.float32), out)
+    with pytest.raises(ValueError):
+        mreg.prefilter_noalloc(out, torch.zeros((H, W), dtype=torch.float32))
+    # the C entry point itself refuses a host address before launching anything
+    host = np.zeros((H, W), np.float32)
+    lib = mreg.load()
+    assert lib.mreg_prefilter_noalloc(host.ctypes.data, W, out.data_ptr(), W, H,
+                                      None) == mreg.MREG_ERR_INVALID_ARG
+    assert b"device memory" in lib.mreg_last_error()
+    assert lib.mreg_prefilter_noalloc(out.data_ptr(), W, host.ctypes.data, W, H,
+                                      None) == mreg.MREG_ERR_INVALID_ARG
+    # and a valid call afterwards still works
+    img = torch.from_numpy(_image(H, W, seed=7)).cuda()
+    mreg.prefilter_noalloc(img, out)
+    torch.cuda.synchronize()
+    ref = bspline.prefilter_2d(img.cpu().numpy())
+    assert np.abs(out.cpu().numpy() - ref).max() <= 5e-6 * np.abs(ref).max()
