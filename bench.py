@@ -15,10 +15,10 @@ graph launch around one persistent kernel, with the team shape chosen by the
 library's autotuner before timing.
 
 The default run (config 1) also times the other forms briefly and reports
-them under "forms": the batched engine on the 256-pair workload (FP32 and
-BF16-stored coefficients), the same pairs through one-pair handles on 8 CUDA
-streams (the plain FP32 form), and the differentiation form (--no-forms
-skips them).  Its line carries "parity": the timed run's final node
+them under "forms": the batched engine on the 256-pair workload (FP32, and
+with BF16- and FP16-stored coefficients), the same pairs through one-pair
+handles on 8 CUDA streams (the plain FP32 form), and the differentiation
+form (--no-forms skips them).  Its line carries "parity": the timed run's final node
 displacements and MSD against one full FP64 oracle registration of the same
 pair.
 
@@ -46,8 +46,10 @@ if ROOT not in sys.path:
 
 from paper_1411_2141_gb300 import inputs  # noqa: E402
 
-MODE_NAMES = {"S0": "explicit Eq.5+Eq.14", "S1": "umbrella-implicit solve (Jacobi-PCG)",
-              "S2": "P1-FEM-implicit solve (Jacobi-PCG)"}
+MODE_NAMES = {"S0": "explicit Eq.5+Eq.14", "S1": "umbrella-implicit solve",
+              "S2": "P1-FEM-implicit solve"}
+SOLVER_NAMES = {"chebyshev": "Jacobi-Chebyshev semi-iteration, verified residual",
+                "cg": "Jacobi-PCG", "none": "no solve"}
 
 
 def parse():
@@ -59,8 +61,13 @@ def parse():
     p.add_argument("--config", type=int, default=1)
     p.add_argument("--mode", default="S1", choices=["S0", "S1", "S2"])
     p.add_argument("--grad", default="G0", choices=["G0", "G1"])
-    p.add_argument("--coeff", default="fp32", choices=["fp32", "bf16"],
-                   help="storage of Te's spline coefficients (bf16: the precision form)")
+    p.add_argument("--solver", default="auto", choices=["auto", "cg", "chebyshev"],
+                   help="linear solve of the semi-implicit forms (auto: Chebyshev for S1, CG for S2)")
+    p.add_argument("--neighbour-sync", action="store_true",
+                   help="synchronise the Chebyshev steps by neighbour blocks instead of the grid "
+                        "barrier (the library's option; measured slower on the 512^2 pair)")
+    p.add_argument("--coeff", default="fp32", choices=["fp32", "bf16", "fp16"],
+                   help="storage of Te's spline coefficients (bf16, fp16: the precision form)")
     p.add_argument("--team", default=None,
                    help="config 3: fixed team shape 'ctas,block[,blocks_per_sm]' instead of "
                         "the autotuner")
@@ -82,20 +89,36 @@ def parse():
 
 
 # ------------------------------------------------------------- bytes model
-def algorithmic_bytes_per_iteration(n_v: int, n_t: int, nnz: int, mode: str, cg_its: float) -> float:
+def algorithmic_bytes_per_iteration(n_v: int, n_t: int, nnz: int, mode: str, cg_its: float,
+                                    solver: str = "cg") -> float:
     """Compulsory bytes of one iteration of the iteration kernel (each array
-    read or written once; gathers of neighbours counted once per node)."""
+    read or written once; gathers of neighbours counted once per node).
+    cg_its: mean iterations (CG) or steps (Chebyshev) of a solve."""
     sample = n_v * (8 + 8 + 4 + 4)                          # V, u, Re(V) in; f out
     force = 4 * (n_v + 1) + 4 * 3 * n_t + 12 * n_t + 8 * n_v  # inc CSR, triangles, F out
     if mode == "S0":
         update = 4 * (n_v + 1) + 4 * nnz + 8 * n_v + 8 * n_v + 8 * n_v  # graph, u0 out/in, u out
         return sample + force + update
     graph = 4 * (n_v + 1) + 4 * nnz
+    if mode == "S1" and solver == "chebyshev":
+        # first phase: graph, x in; b out, previous b in (verification); d, x' out; 1/diag(A)
+        first = graph + 8 * n_v + 16 * n_v + 16 * n_v + 8 * n_v + 8 * n_v + 4 * n_v
+        # each further step: graph, x and b in, d in and out, 1/diag(A), x' out
+        step = graph + 8 * n_v + 16 * n_v + 16 * n_v + 4 * n_v + 8 * n_v
+        return sample + force + first + max(cg_its - 1.0, 0.0) * step
     vals = (8 * nnz + 8 * n_v) if mode == "S2" else 0
     init = graph + vals + 8 * n_v + 16 * n_v + 8 * n_v + 8 * n_v + 4 * n_v   # u, b, r, z out, dinv
     cg1 = graph + vals / 2 + 8 * n_v * 3 + 16 * n_v + 8 * n_v * 3           # z, p, x, b in; p', q, rt out
     cg2 = 8 * n_v * 4 + 4 * n_v + 8 * n_v * 3                                # p, q, x, r in; x, r, z out
     return sample + force + init + cg_its * (cg1 + cg2)
+
+
+def solver_of(args) -> str:
+    """The linear solver the run uses: the library's default is Chebyshev
+    semi-iteration for S1 and CG for S2 (--solver overrides)."""
+    if args.mode == "S1" and args.solver in ("auto", "chebyshev"):
+        return "chebyshev"
+    return "cg" if args.mode != "S0" else "none"
 
 
 # ------------------------------------------------------------------ clocks
@@ -235,7 +258,7 @@ def launches_per_registration(args, n_iter: int) -> int:
     1024-iteration chunk, the warp's per-triangle affine records, warp + MSD
     and the final MSD sum."""
     chunks = (n_iter + 1023) // 1024
-    return (4 + (args.coeff == "bf16") + 1 + 2 + 2 * chunks + 3)
+    return (4 + (args.coeff != "fp32") + 1 + 2 + 2 * chunks + 3)
 
 
 def run_reference_adjoint(args):
@@ -298,12 +321,13 @@ def run_reference_batch(args):
 def workload_config(args, case):
     s = case.spec
     return {"workload": f"config{args.config}: {s.side}x{s.side} pair, {case.n_nodes}-node mesh, "
-                        f"{s.n_iter} iterations, {args.mode} {MODE_NAMES[args.mode]}, "
+                        f"{s.n_iter} iterations, {args.mode} {MODE_NAMES[args.mode]}"
+                        f"{' (' + SOLVER_NAMES[solver_of(args)] + ')' if args.mode != 'S0' else ''}, "
                         f"{args.grad} {'mesh gradient Eq.9-10' if args.grad == 'G0' else 'spline gradient'}"
-                        + (", BF16-stored Te coefficients" if args.coeff == "bf16" else ""),
+                        + (f", {args.coeff.upper()}-stored Te coefficients" if args.coeff != "fp32" else ""),
             "image": [s.side, s.side], "nodes": case.n_nodes, "triangles": case.n_tris,
             "iterations": s.n_iter, "mode": args.mode, "grad": args.grad, "coeff": args.coeff,
-            "alpha": s.alpha, "tau": s.tau,
+            "solver": solver_of(args), "alpha": s.alpha, "tau": s.tau,
             "l2": "flushed between timed steps (256 MiB write); the step's own working set is L2-resident",
             "parallelism": f"replicas x{args.gpus} (one pair per GPU per step)"}
 
@@ -384,9 +408,10 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     Re_d = torch.from_numpy(case.Re).to(dev)
     Te_d = torch.from_numpy(case.Te).to(dev)
-    bf16 = args.coeff == "bf16"
+    coeff = args.coeff
     reg = mreg.Registration(case.V, case.T, Re_d, Te_d, spec.alpha, spec.tau,
-                            mode=args.mode, grad=args.grad, coeff_bf16=bf16, stream=stream)
+                            mode=args.mode, grad=args.grad, coeff=coeff, solver=args.solver,
+                            neighbour_sync=args.neighbour_sync, stream=stream)
     msd_dev = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -443,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
 
         def e2e_once():
             with mreg.Registration(case.V, case.T, Re_h, Te_h, spec.alpha, spec.tau,
-                                   mode=args.mode, grad=args.grad, coeff_bf16=bf16,
+                                   mode=args.mode, grad=args.grad, coeff=coeff, solver=args.solver,
                                    stream=stream, allocator=alloc) as r:
                 r.step(n_iter, stream)
                 m = r.msd(stream)
@@ -472,7 +497,8 @@ def run_ours(args, rank, world, local_rank):
     value = whole_job_rate(args.steps, world, total_s)
     e = np.sort(np.concatenate([case.T[:, [0, 1]], case.T[:, [1, 2]], case.T[:, [2, 0]]]), axis=1)
     nnz = 2 * len(np.unique(e, axis=0))          # off-diagonal entries of the node graph
-    per_iter = algorithmic_bytes_per_iteration(case.n_nodes, case.n_tris, nnz, args.mode, cg_mean)
+    per_iter = algorithmic_bytes_per_iteration(case.n_nodes, case.n_tris, nnz, args.mode, cg_mean,
+                                               solver_of(args))
     it_ms = statistics.mean(iter_ms)
     achieved = per_iter * n_iter / (it_ms / 1e3) / 1e9
     peak, peak_src = peak_hbm()
@@ -536,7 +562,9 @@ def batch_workload_config(args, cases, shape=None):
     n_iter = cases[0].spec.n_iter
     cfg = {"workload": f"config3: batch of {len(cases)} pairs, sides {min(sides)}-{max(sides)} px "
                        f"(log-uniform), {min(nodes)}-{max(nodes)} nodes ({sum(nodes)} total), "
-                       f"{n_iter} iterations each, {args.mode} {MODE_NAMES[args.mode]}, {args.grad}",
+                       f"{n_iter} iterations each, {args.mode} {MODE_NAMES[args.mode]}"
+                       f"{' (' + SOLVER_NAMES[solver_of(args)] + ')' if args.mode != 'S0' else ''}, "
+                       f"{args.grad}",
            "pairs": len(cases), "pixels": int(sum(s * s for s in sides)), "nodes": int(sum(nodes)),
            "triangles": int(sum(c.n_tris for c in cases)), "iterations": n_iter,
            "mode": args.mode, "grad": args.grad, "coeff": args.coeff,
@@ -582,7 +610,7 @@ def run_ours_batch_single(args, rank, world, local_rank, cases=None):
     stream = torch.cuda.current_stream()
     regs = [mreg.Registration(c.V, c.T, torch.from_numpy(c.Re).to(dev),
                               torch.from_numpy(c.Te).to(dev), c.spec.alpha, c.spec.tau,
-                              mode=args.mode, grad=args.grad, coeff_bf16=args.coeff == "bf16",
+                              mode=args.mode, grad=args.grad, coeff=args.coeff, solver=args.solver,
                               stream=stream) for c in cases]
     msd_dev = torch.empty(len(cases), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -654,17 +682,18 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
     cases = cases or batch_cases(args.pairs)
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
-    bf16 = args.coeff == "bf16"
+    coeff = args.coeff
     pairs = [(c.V, c.T, c.Re, c.Te) for c in cases]
     b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode, grad=args.grad,
-                   coeff_bf16=bf16, stream=stream)
+                   coeff=coeff, solver=args.solver, stream=stream)
     if args.team:
         vals = [int(x) for x in args.team.split(",")]
         ctas, block, per_sm = (vals + [1])[:3]
         b.close()
         b = mreg.Batch(pairs, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
-                       grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
-                       team_blocks_per_sm=per_sm, grid_blocks=args.teams, stream=stream)
+                       grad=args.grad, coeff=coeff, team_ctas=ctas, block_size=block,
+                       team_blocks_per_sm=per_sm, grid_blocks=args.teams, solver=args.solver,
+                       stream=stream)
         tune_s, tune_ms = 0.0, {}
     else:
         t0 = time.perf_counter()
@@ -706,7 +735,8 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
         e = np.sort(np.concatenate([c.T[:, [0, 1]], c.T[:, [1, 2]], c.T[:, [2, 0]]]), axis=1)
         nnz = 2 * len(np.unique(e, axis=0))
         nnz_total += nnz
-        per_iter_total += algorithmic_bytes_per_iteration(c.n_nodes, c.n_tris, nnz, args.mode, cgm)
+        per_iter_total += algorithmic_bytes_per_iteration(c.n_nodes, c.n_tris, nnz, args.mode, cgm,
+                                                          solver_of(args))
 
     e2e = None
     if not args.no_e2e:
@@ -717,8 +747,9 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
 
         def e2e_once():
             with mreg.Batch(pinned, cases[0].spec.alpha, cases[0].spec.tau, mode=args.mode,
-                            grad=args.grad, coeff_bf16=bf16, team_ctas=ctas, block_size=block,
-                            team_blocks_per_sm=per_sm, stream=stream, allocator=alloc) as bb:
+                            grad=args.grad, coeff=coeff, team_ctas=ctas, block_size=block,
+                            team_blocks_per_sm=per_sm, solver=args.solver, stream=stream,
+                            allocator=alloc) as bb:
                 bb.run(n_iter, stream)
                 m = bb.msd(stream)
                 us = [bb.get_u(k, stream) for k in range(len(cases))]
@@ -986,12 +1017,13 @@ def run_forms(args, rank, world, local_rank) -> dict | None:
             line, "config 3: 256 uneven pairs, 100 iterations each, batched engine (one CUDA-graph "
                   "launch, autotuned team shape), FP32")
         sub.team = ",".join(str(x) for x in line["autotune"]["chosen"])
-    sub.coeff = "bf16"
-    line = run_ours_batch(sub, rank, world, local_rank, cases)
-    if line is not None:
-        forms["batched_bf16"] = _form_summary(
-            line, "the same batch with BF16-stored Te coefficients (the precision form), the team "
-                  "shape the FP32 run's autotuner chose")
+    for storage in ("bf16", "fp16"):
+        sub.coeff = storage
+        line = run_ours_batch(sub, rank, world, local_rank, cases)
+        if line is not None:
+            forms[f"batched_{storage}"] = _form_summary(
+                line, f"the same batch with {storage.upper()}-stored Te coefficients (the precision "
+                      f"form), the team shape the FP32 run's autotuner chose")
     sub.coeff, sub.team = "fp32", None
     line = run_ours_batch_single(sub, rank, world, local_rank, cases)
     if line is not None:

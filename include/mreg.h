@@ -88,6 +88,30 @@ enum {
                                    needs MREG_GRAD_SPLINE                    */
 };
 
+/* Storage of Te's spline coefficients (mreg_options.coeff_storage). */
+enum {
+  MREG_COEFF_FP32 = 0,
+  MREG_COEFF_BF16 = 1,   /* 8 significant bits                               */
+  MREG_COEFF_FP16 = 2    /* IEEE half: 11 significant bits, |c| < 65504       */
+};
+
+/* Linear solver of the semi-implicit forms (mreg_options.solver).
+ *   CG: Jacobi-preconditioned conjugate gradients in the single-reduction
+ *       form of Chronopoulos and Gear (one inner-product reduction per
+ *       iteration).
+ *   CHEBYSHEV (S1 only): Chebyshev semi-iteration on the Jacobi-scaled
+ *       system, whose spectrum lies in [1/(1+l), (1+2l)/(1+l)] for the
+ *       umbrella form (the random-walk matrix D_m^-1 W has its spectrum in
+ *       [-1, 1]); no inner products inside the solve.  The step count comes
+ *       from the a-priori Chebyshev bound and ||r_0|| / ||b||, and every
+ *       solve's true residual is verified against pcg_rtol (a solve that
+ *       misses it is continued).                                           */
+enum {
+  MREG_SOLVER_AUTO = 0,
+  MREG_SOLVER_CG = 1,
+  MREG_SOLVER_CHEBYSHEV = 2
+};
+
 /* Where the iteration loop of one pair runs (the batched engine is the
  * mreg_batch_* API). */
 enum {
@@ -136,13 +160,16 @@ typedef struct {
                           the mesh has more nodes than 256 per SM, else 256 */
   int32_t grid_blocks; /* blocks of the iteration kernel; 0 = automatic     */
   int32_t engine;      /* MREG_ENGINE_*                     (default AUTO)  */
-  int32_t coeff_bf16;  /* 1: the iteration and the warp read Te's B-spline
-                          coefficients from a BF16 copy (round to nearest
-                          even of the FP32 prefilter output); every sum and
+  int32_t coeff_storage; /* MREG_COEFF_*: storage of Te's B-spline
+                          coefficients that the iteration and the warp read.
+                          BF16 / FP16: a 16-bit copy (round to nearest even
+                          of the FP32 prefilter output); every sum and
                           product stays FP32 and the reductions keep their
                           precision.  Halves the coefficient footprint; the
-                          error this adds is stated against the FP64 method,
-                          not bounded by the FP32 tolerances.  (default 0)  */
+                          error this adds is the storage format's own (the
+                          exact method on the rounded coefficients shows the
+                          same), stated against the FP64 method, not bounded
+                          by the FP32 tolerances.          (default FP32)  */
   int32_t team_ctas;   /* batched engine only: CTAs per team (one thread-block
                           cluster registers one pair at a time): 1, 2, 4, 8
                           or 16 (16 is a non-portable cluster size); 0 = 4.
@@ -171,6 +198,20 @@ typedef struct {
                           pair fits the grid (at most 256 nodes per SM, the
                           block then 512 threads), else 1.  Other modes and
                           engines accept 0 or 1.                            */
+  int32_t solver;      /* linear solve of the semi-implicit forms:
+                          MREG_SOLVER_AUTO (0): Chebyshev for S1, CG for S2;
+                          MREG_SOLVER_CG (1); MREG_SOLVER_CHEBYSHEV (2, S1
+                          only).  Both stop at the same verified residual
+                          (pcg_rtol); pcg_maxit caps the iterations (CG) or
+                          steps (Chebyshev) of one solve.                   */
+  int32_t neighbour_sync; /* grid engine, Chebyshev solve: 1 = its steps,
+                          whose only cross-block reads are 1-ring values,
+                          synchronise each block with the blocks that own
+                          its nodes' neighbours (bounded waits on per-block
+                          flags) instead of with the whole grid, when no
+                          block has more than 32 such blocks; 0 (default) =
+                          the grid barrier throughout (measured faster on
+                          GB300 for the 512^2 / 20k-node pair).             */
   /* Device memory.  With alloc non-NULL every device buffer of the handle or
    * batch comes from alloc(bytes, stream, alloc_ctx) -- stream being the
    * stream of the call that allocates -- and goes back through
@@ -187,7 +228,8 @@ typedef struct {
 
 typedef struct {
   int32_t iterations_done;     /* total iterations since create / reset     */
-  int32_t last_pcg_iters;      /* CG iterations of the last solve (S1/S2)    */
+  int32_t last_pcg_iters;      /* iterations (CG) or steps (Chebyshev) of the
+                                  last solve (S1/S2)                         */
   int32_t max_pcg_iters;       /* largest count since create / reset         */
   int32_t not_converged;       /* solves that stopped at the cap             */
   double last_rel_resid;       /* ||b - A u'|| / ||b|| of the last solve, max
@@ -199,6 +241,8 @@ typedef struct {
   int32_t device_status;       /* raw device status bits (0 = clean)         */
   int32_t engine;              /* MREG_ENGINE_GRID                            */
   int32_t node_lanes;          /* lanes per node of the iteration kernel      */
+  int32_t neighbour_sync;      /* 1 when the Chebyshev steps use the
+                                  neighbour synchronisation                  */
 } mreg_stats_t;
 
 /* Fields readable with mreg_get_field (mainly for parity tests). */
@@ -219,9 +263,10 @@ enum {
   MREG_FIELD_PCG_RESID = 9,  /* n double: final relative residual of each
                                 solve of the last mreg_step call (as
                                 mreg_stats_t.last_rel_resid)                  */
-  MREG_FIELD_COEF_TE_BF16 = 10 /* H x W uint16: the BF16 copy of Te's
-                                coefficients (bit patterns); 0 elements when
-                                coeff_bf16 is off                             */
+  MREG_FIELD_COEF_TE_16 = 10 /* H x W uint16: the 16-bit copy of Te's
+                                coefficients (BF16 or FP16 bit patterns, as
+                                coeff_storage says); 0 elements with FP32
+                                storage                                       */
 };
 
 /* Fill *opts with the defaults listed in mreg_options. */
@@ -334,6 +379,20 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
  * MREG_ERR_NOT_CONVERGED if a solve hit its cap since the last reset, else
  * MREG_OK.  out may be NULL.                                                */
 mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream);
+
+/* The system matrix of the semi-implicit step applied to a vector:
+ *   y = A x,  A = (1+l) D_m - l W (S1: the umbrella form of the diffusion of
+ *   Eq. 7 with Eq. 11-13), or A = M + l K (S2: P1 mass and stiffness of
+ *   Eq. 1 on the undeformed mesh, the FP32 entries the solver uses).
+ * The iteration kernel fuses this product into its solver phases; this is
+ * the same sparse matrix-vector product on its own (for residuals of a
+ * caller's own solves, or operator checks).
+ *   x_dev, y_dev  device n_nodes x 2 float (x and y components per node,
+ *                 node order of the mesh); must not be the same buffer
+ * FP32 arithmetic, each row summed in ascending column order (bitwise
+ * repeatable).  Errors: INVALID_ARG for NULL pointers, x == y, or the
+ * explicit mode (S0 has no system matrix).  Asynchronous.                   */
+mreg_status mreg_apply_operator(mreg_handle* h, const float* x_dev, float* y_dev, void* stream);
 
 /* Release every resource of the handle (after the handle's work finished).
  * NULL is accepted.                                                         */
@@ -452,6 +511,13 @@ mreg_status mreg_batch_get_field(mreg_batch* b, int32_t pair, int32_t field, voi
 
 /* Solver state of one pair after the last run (as mreg_stats). Blocks.     */
 mreg_status mreg_batch_stats(mreg_batch* b, int32_t pair, mreg_stats_t* out, void* stream);
+
+/* mreg_apply_operator for every pair of the batch in one launch: x_dev and
+ * y_dev hold n_nodes x 2 floats of every pair, packed in pair order (pair p
+ * starts at the sum of the node counts of the pairs before it).  The first
+ * call allocates 8 bytes per 256 nodes of block table.  Asynchronous.      */
+mreg_status mreg_batch_apply_operator(mreg_batch* b, const float* x_dev, float* y_dev,
+                                      void* stream);
 
 /* Release everything (after the batch's work finished).  NULL is accepted. */
 void mreg_batch_destroy(mreg_batch* b);

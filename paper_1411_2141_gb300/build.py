@@ -20,7 +20,7 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libmreg.so")
 
 SOURCES = ["api.cpp", "batch_api.cpp", "prefilter.cu", "iterate.cu",
-           "batch.cu", "warp.cu", "topology.cu", "prefilter_noalloc.cu"]
+           "batch.cu", "warp.cu", "topology.cu", "operator.cu", "prefilter_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

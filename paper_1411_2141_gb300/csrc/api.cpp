@@ -266,6 +266,11 @@ struct mreg_handle {
   int form = 0, grad = 0;
   int grid = 0, block = 0, warp_grid = 0;
   int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
+  bool cheb = false;   // S1 solved by Chebyshev semi-iteration
+  bool nsync = false;  // its steps use the neighbour synchronisation
+  unsigned* nflags = nullptr;
+  int *nbr_idx = nullptr, *nbr_cnt = nullptr;
+  float cheb_par[4] = {1.0f, 1.0f, 0.0f, 1.0f};   // theta, delta, acosh(theta/delta), scale
   int lanes = 1;  // lanes per node of the iteration kernel
   int engine = MREG_ENGINE_GRID;
   float area_floor = 0.0f;
@@ -277,7 +282,8 @@ struct mreg_handle {
   void* arena = nullptr;
   // device arrays
   float *Re = nullptr, *Te = nullptr, *cRe = nullptr, *cTe = nullptr, *tmp = nullptr;
-  __nv_bfloat16* cTe16 = nullptr;   // BF16 copy of cTe (coeff_bf16 only)
+  __nv_bfloat16* cTe16 = nullptr;   // BF16 copy of cTe (BF16 storage only)
+  __half* cTeh = nullptr;           // FP16 copy of cTe (FP16 storage only)
   int* pix_tri = nullptr;
   float2* V = nullptr;
   int *tri = nullptr, *inc_ptr = nullptr;
@@ -326,6 +332,10 @@ struct mreg_handle {
     a.lam = (float)lam;
     a.area_floor = area_floor;
     a.rtol2 = (float)(opts.pcg_rtol * opts.pcg_rtol);
+    a.cheb_theta = cheb_par[0];
+    a.cheb_delta = cheb_par[1];
+    a.cheb_acosh = cheb_par[2];
+    a.cheb_scale = cheb_par[3];
     a.tau_ff = make_float2((float)tau, (float)(tau - (double)(float)tau));
     a.lam_ff = make_float2((float)lam, (float)(lam - (double)(float)lam));
     a.V = V;
@@ -344,6 +354,7 @@ struct mreg_handle {
     a.lumped = lumped;
     a.cTe = cTe;
     a.cTe16 = cTe16;
+    a.cTeh = cTeh;
     a.ReV = ReV;
     a.ReQ = ReQ;
     a.u_keep = u_keep ? u_keep + (size_t)it0 * nV : nullptr;
@@ -360,6 +371,9 @@ struct mreg_handle {
     a.bar = bar;
     a.status = status;
     a.barrier_timeout_ns = stall_barrier > 0 ? stall_timeout_ns : mreg::kBarrierTimeoutNs;
+    a.nflags = nsync ? nflags : nullptr;
+    a.nbr_idx = nbr_idx;
+    a.nbr_cnt = nbr_cnt;
     a.stall_block = stall_block;
     a.stall_barrier = stall_barrier;
     a.energy_hist = energy_hist;
@@ -398,6 +412,33 @@ mreg_status validate_image(const mreg_image* im, const char* name) {
   return MREG_OK;
 }
 
+// The spectrum of D^-1 A for S1 lies in [1/(1+l), (1+2l)/(1+l)] (the
+// random-walk matrix D_m^-1 W has its spectrum in [-1, 1]); the interval is
+// widened by 1e-5 relative, far more than the FP32 rounding of the Jacobi
+// entries moves it (and so that l = 0 gives a non-empty interval).  The step
+// count uses the bound with sqrt(m_max / m_min) (the change from the
+// D^-1/2-weighted norm to the 2-norm) over a safety margin of 1/2.
+void chebyshev_params(double lam, int m_min, int m_max, float out[4]) {
+  const double lo = (1.0 / (1.0 + lam)) * (1.0 - 1e-5);
+  const double hi = ((1.0 + 2.0 * lam) / (1.0 + lam)) * (1.0 + 1e-5);
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  out[0] = (float)theta;
+  out[1] = (float)delta;
+  out[2] = (float)std::acosh(theta / delta);
+  out[3] = (float)(std::sqrt((double)std::max(m_max, 1) / (double)std::max(m_min, 1)) / 0.5);
+}
+
+void valence_range(const int* ptr, int n, int* m_min, int* m_max) {
+  int lo = n > 0 ? ptr[1] - ptr[0] : 1, hi = lo;
+  for (int i = 1; i < n; ++i) {
+    const int m = ptr[i + 1] - ptr[i];
+    lo = std::min(lo, m);
+    hi = std::max(hi, m);
+  }
+  *m_min = lo;
+  *m_max = hi;
+}
+
 mreg_status validate_options(const mreg_options& o, double alpha, double tau, double* lam) {
   if (o.mode < 0 || o.mode > 2) return fail(MREG_ERR_INVALID_ARG, "unknown mode %d", o.mode);
   if (o.grad < 0 || o.grad > 1) return fail(MREG_ERR_INVALID_ARG, "unknown grad %d", o.grad);
@@ -413,8 +454,8 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.grid_blocks < 0) return fail(MREG_ERR_INVALID_ARG, "grid_blocks must be >= 0");
   if (o.engine != MREG_ENGINE_AUTO && o.engine != MREG_ENGINE_GRID)
     return fail(MREG_ERR_INVALID_ARG, "unknown engine %d", o.engine);
-  if (o.coeff_bf16 != 0 && o.coeff_bf16 != 1)
-    return fail(MREG_ERR_INVALID_ARG, "coeff_bf16 must be 0 or 1");
+  if (o.coeff_storage < MREG_COEFF_FP32 || o.coeff_storage > MREG_COEFF_FP16)
+    return fail(MREG_ERR_INVALID_ARG, "coeff_storage must be 0 (FP32), 1 (BF16) or 2 (FP16)");
   if (o.team_blocks_per_sm < 0 || o.team_blocks_per_sm > 2)
     return fail(MREG_ERR_INVALID_ARG, "team_blocks_per_sm must be 0, 1 or 2");
   if (o.host_topology != 0 && o.host_topology != 1)
@@ -428,6 +469,12 @@ mreg_status validate_options(const mreg_options& o, double alpha, double tau, do
   if (o.node_lanes == 2 && (o.mode == MREG_MODE_EXPLICIT || o.team_blocks_per_sm == 2))
     return fail(MREG_ERR_INVALID_ARG,
                 "node_lanes 2 needs an implicit mode with team_blocks_per_sm 1");
+  if (o.neighbour_sync != 0 && o.neighbour_sync != 1)
+    return fail(MREG_ERR_INVALID_ARG, "neighbour_sync must be 0 or 1");
+  if (o.solver < MREG_SOLVER_AUTO || o.solver > MREG_SOLVER_CHEBYSHEV)
+    return fail(MREG_ERR_INVALID_ARG, "unknown solver %d", o.solver);
+  if (o.solver == MREG_SOLVER_CHEBYSHEV && o.mode != MREG_MODE_UMBRELLA_IMPLICIT)
+    return fail(MREG_ERR_INVALID_ARG, "the Chebyshev solve is for the umbrella-implicit mode (S1)");
   const double l = o.lambda < 0.0 ? tau * alpha : o.lambda;
   if (!std::isfinite(l)) return fail(MREG_ERR_INVALID_ARG, "lambda is not finite");
   *lam = l;
@@ -468,6 +515,8 @@ mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
   CK(mreg::launch_prefilter(h->Te, h->W, h->tmp, h->cTe, h->W, h->H, s), "prefilter Te");
   if (h->cTe16)
     CK(mreg::launch_to_bf16(h->cTe, (int64_t)h->W * h->H, h->cTe16, s), "BF16 coefficients");
+  if (h->cTeh)
+    CK(mreg::launch_to_fp16(h->cTe, (int64_t)h->W * h->H, h->cTeh, s), "FP16 coefficients");
   CK(mreg::launch_sample_nodes(h->cRe, h->W, h->H, h->V, h->nV, h->ReV, s), "Re at nodes");
   if (h->form == mreg::kFormFemEdges)
     CK(mreg::launch_sample_edges(h->cRe, h->W, h->H, h->V, h->edges, h->nE, h->ReQ, s),
@@ -594,7 +643,9 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                           : (o.mode != MREG_MODE_EXPLICIT && h->minb == 1 && small_mesh ? 2 : 1);
   h->block = o.block_size ? o.block_size : (h->lanes == 2 || !small_mesh ? 512 : 256);
   int per_sm = 0;
-  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, h->minb, h->lanes, &per_sm), "occupancy");
+  h->cheb = use_chebyshev(o);
+  CK(mreg::iterate_max_blocks(h->form, h->grad, h->block, h->minb, h->lanes, h->cheb, &per_sm),
+     "occupancy");
   if (per_sm < 1) return fail(MREG_ERR_INVALID_ARG, "block_size %d does not fit on an SM", h->block);
   const int max_grid = per_sm * h->num_sms;
   const int want = (int)(((int64_t)h->nV * h->lanes + h->block - 1) / h->block);
@@ -631,7 +682,9 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
                o_wp = take((size_t)h->warp_grid * mreg::kRec * 4), o_aff = take(nT * 32),
                o_msd = take(8), o_cnt = take(16),
                o_ep = take((size_t)(kChunk + 1) * ((h->grid * h->block + 31) / 32) * 8),
-               o_c16 = take(o.coeff_bf16 ? npx * 2 : 0);
+               o_c16 = take(o.coeff_storage != MREG_COEFF_FP32 ? npx * 2 : 0),
+               o_nbr = take((size_t)h->grid * mreg::kMaxNbr * 4), o_ncnt = take((size_t)h->grid * 4),
+               o_nflag = take((size_t)h->grid * 4);
   h->mem.alloc = o.alloc;
   h->mem.free = o.free;
   h->mem.ctx = o.alloc_ctx;
@@ -683,7 +736,11 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   h->msd = (double*)(base + o_msd);
   h->counters = (int*)(base + o_cnt);
   h->epart = (float2*)(base + o_ep);
-  h->cTe16 = o.coeff_bf16 ? (__nv_bfloat16*)(base + o_c16) : nullptr;
+  h->cTe16 = o.coeff_storage == MREG_COEFF_BF16 ? (__nv_bfloat16*)(base + o_c16) : nullptr;
+  h->cTeh = o.coeff_storage == MREG_COEFF_FP16 ? (__half*)(base + o_c16) : nullptr;
+  h->nbr_idx = (int*)(base + o_nbr);
+  h->nbr_cnt = (int*)(base + o_ncnt);
+  h->nflags = (unsigned*)(base + o_nflag);
 
   st = upload_image(h, Re, h->Re, s, "Re");
   if (st) return st;
@@ -745,6 +802,29 @@ mreg_status mreg_create(const mreg_mesh* mesh, const mreg_image* Re, const mreg_
   CK(up(h->Aoff, hm.Aoff.data(), (size_t)hm.nnz * 4), "upload");
   CK(up(h->dinv, hm.dinv.data(), nV * 4), "upload");
   }
+  if (h->cheb) {   // the valence range enters the Chebyshev step count
+    int m_min = 1, m_max = 1;
+    if (dev_topo) {
+      std::vector<int> ptr((size_t)nV + 1);
+      CK(cudaMemcpyAsync(ptr.data(), h->adj_ptr, ptr.size() * 4, cudaMemcpyDeviceToHost, s),
+         "copy");
+      CK(cudaStreamSynchronize(s), "synchronize");
+      valence_range(ptr.data(), (int)nV, &m_min, &m_max);
+    } else {
+      valence_range(hm.adj_ptr.data(), (int)nV, &m_min, &m_max);
+    }
+    chebyshev_params(lam, m_min, m_max, h->cheb_par);
+    // neighbour lists of the launch shape: the Chebyshev steps wait only on
+    // the blocks that own their nodes' neighbours, when every list fits
+    CK(mreg::launch_neighbour_blocks(h->adj_ptr, h->adj_col, h->nV, h->grid, h->block, h->lanes,
+                                     h->nbr_idx, h->nbr_cnt, s),
+       "neighbour lists");
+    std::vector<int> cnt((size_t)h->grid);
+    CK(cudaMemcpyAsync(cnt.data(), h->nbr_cnt, cnt.size() * 4, cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    h->nsync = o.neighbour_sync == 1 &&
+               *std::max_element(cnt.begin(), cnt.end()) <= mreg::kMaxNbr;
+  }
   st = device_setup(h, s, true);
   if (st) return st;
   guard.keep = true;
@@ -772,7 +852,7 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
     const mreg::IterArgs a = h->iter_args(n, it0);
     h->stall_block = -1;   // an armed stall applies to one launch only
     h->stall_barrier = 0;
-    CK(mreg::launch_iterate(h->form, h->grad, h->minb, h->lanes, a, h->grid, h->block,
+    CK(mreg::launch_iterate(h->form, h->grad, h->minb, h->lanes, h->cheb, a, h->grid, h->block,
                             (cudaStream_t)stream),
        "iteration kernel launch");
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
@@ -802,6 +882,7 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
   a.u = (const float2*)u_dev;
   a.cTe = h->cTe;
   a.cTe16 = h->cTe16;
+  a.cTeh = h->cTeh;
   a.Re = h->Re;
   a.part = h->warp_part;
   float2* rg = (float2*)h->adj_buf;
@@ -864,6 +945,7 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   a.adj_col = h->adj_col;
   a.cTe = h->cTe;
   a.cTe16 = h->cTe16;
+  a.cTeh = h->cTeh;
   a.ReV = h->ReV;
   const int passes = h->opts.smooth_passes > 0 ? h->opts.smooth_passes : 1;
   CK(mreg::launch_unroll_adjoint(a, ustates, n_iters, passes, va, vb, vc, h->bar, h->status,
@@ -891,6 +973,7 @@ mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* str
   a.u = h->u;
   a.cTe = h->cTe;
   a.cTe16 = h->cTe16;
+  a.cTeh = h->cTeh;
   a.Re = h->Re;
   a.out = out_dev;
   a.part = h->warp_part;
@@ -983,7 +1066,11 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
     case MREG_FIELD_ENERGY: src = h->energy_hist, count = hist, esize = 8; break;
     case MREG_FIELD_PCG_ITERS: src = h->pcg_it_hist, count = hist; break;
     case MREG_FIELD_PCG_RESID: src = h->pcg_res_hist, count = hist, esize = 8; break;
-    case MREG_FIELD_COEF_TE_BF16: src = h->cTe16, count = h->cTe16 ? npx : 0, esize = 2; break;
+    case MREG_FIELD_COEF_TE_16:
+      src = h->cTeh ? (const void*)h->cTeh : (const void*)h->cTe16;
+      count = (h->cTe16 || h->cTeh) ? npx : 0;
+      esize = 2;
+      break;
     default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
   }
   if (count_out) *count_out = count;
@@ -1019,6 +1106,7 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
     out->device_status = status;
     out->engine = h->engine;
     out->node_lanes = h->lanes;
+    out->neighbour_sync = h->nsync ? 1 : 0;
   }
   if (status & mreg::kStatusBarrierTimeout) {
     h->device_failed = true;
@@ -1027,6 +1115,18 @@ mreg_status mreg_stats(mreg_handle* h, mreg_stats_t* out, void* stream) {
   if (status & mreg::kStatusNotConverged)
     return fail(MREG_ERR_NOT_CONVERGED, "%d solves stopped at the CG iteration cap (%d)",
                 (int)last[4], h->opts.pcg_maxit);
+  return MREG_OK;
+}
+
+mreg_status mreg_apply_operator(mreg_handle* h, const float* x_dev, float* y_dev, void* stream) {
+  if (!h || !x_dev || !y_dev) return fail(MREG_ERR_INVALID_ARG, "handle, x or y is NULL");
+  if (h->form == mreg::kFormExplicit)
+    return fail(MREG_ERR_INVALID_ARG, "the explicit mode has no system matrix");
+  if (x_dev == y_dev) return fail(MREG_ERR_INVALID_ARG, "x and y must not be the same buffer");
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  CK(mreg::launch_apply_operator(h->form, h->iter_args(0, 0), (const float2*)x_dev, (float2*)y_dev,
+                                 h->num_sms, (cudaStream_t)stream),
+     "operator kernel launch");
   return MREG_OK;
 }
 

@@ -143,12 +143,13 @@ struct ClusterTeam {
     else cgrp::this_cluster().sync();
     return true;
   }
+  __device__ __forceinline__ bool sync_local() { return sync(); }
 };
 
 // MINB: CTAs per SM the register budget is sized for (1: up to 128
 // registers per thread; 2: up to 64 for 512-thread CTAs, the rest spilled
 // to local memory).  The autotuner picks between them.
-template <int FORM, int GRAD, int MINB>
+template <int FORM, int GRAD, int MINB, bool CHEB>
 __global__ void __launch_bounds__(kIterBlockMax, MINB) k_batch(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) IterArgs s_a;
@@ -184,6 +185,9 @@ __global__ void __launch_bounds__(kIterBlockMax, MINB) k_batch(const BatchArgs b
     __syncthreads();
     if constexpr (FORM == kFormExplicit) {
       run_explicit<GRAD>(s_a, team, dsm);
+    } else if constexpr (CHEB) {
+      static_assert(FORM == kFormUmbrella, "the Chebyshev solve is the S1 form's");
+      run_chebyshev<GRAD, 1>(s_a, team, dsm);
     } else {
       run_implicit<FORM, GRAD>(s_a, team, dsm);
     }
@@ -255,21 +259,27 @@ __global__ void k_batch_msd(const BatchWarpArgs b) {
 }
 
 template <int MINB>
-void* select_batch_kernel_m(int form, int grad) {
+void* select_batch_kernel_m(int form, int grad, bool cheb) {
+  if (cheb) {
+    if (form != kFormUmbrella) return nullptr;
+    return grad ? (void*)k_batch<kFormUmbrella, 1, MINB, true>
+                : (void*)k_batch<kFormUmbrella, 0, MINB, true>;
+  }
   switch (form * 2 + (grad ? 1 : 0)) {
-    case 0: return (void*)k_batch<kFormExplicit, 0, MINB>;
-    case 1: return (void*)k_batch<kFormExplicit, 1, MINB>;
-    case 2: return (void*)k_batch<kFormUmbrella, 0, MINB>;
-    case 3: return (void*)k_batch<kFormUmbrella, 1, MINB>;
-    case 4: return (void*)k_batch<kFormFemNodes, 0, MINB>;
-    case 5: return (void*)k_batch<kFormFemNodes, 1, MINB>;
-    case 7: return (void*)k_batch<kFormFemEdges, 1, MINB>;
+    case 0: return (void*)k_batch<kFormExplicit, 0, MINB, false>;
+    case 1: return (void*)k_batch<kFormExplicit, 1, MINB, false>;
+    case 2: return (void*)k_batch<kFormUmbrella, 0, MINB, false>;
+    case 3: return (void*)k_batch<kFormUmbrella, 1, MINB, false>;
+    case 4: return (void*)k_batch<kFormFemNodes, 0, MINB, false>;
+    case 5: return (void*)k_batch<kFormFemNodes, 1, MINB, false>;
+    case 7: return (void*)k_batch<kFormFemEdges, 1, MINB, false>;
     default: return nullptr;
   }
 }
 
-void* select_batch_kernel(int form, int grad, int minb) {
-  return minb == 2 ? select_batch_kernel_m<2>(form, grad) : select_batch_kernel_m<1>(form, grad);
+void* select_batch_kernel(int form, int grad, int minb, bool cheb) {
+  return minb == 2 ? select_batch_kernel_m<2>(form, grad, cheb)
+                   : select_batch_kernel_m<1>(form, grad, cheb);
 }
 
 int grid_for(int64_t n, int block) {
@@ -281,7 +291,7 @@ int grid_for(int64_t n, int block) {
 
 // Function attributes are set here, outside any stream capture; the
 // launchers below only enqueue work (they may be recorded into a graph).
-cudaError_t batch_prepare(int form, int grad, int block, int minb) {
+cudaError_t batch_prepare(int form, int grad, int block, int minb, bool cheb) {
   const size_t smem = kSmemPerWarp * kSetupWarps;
   cudaError_t e = cudaFuncSetAttribute(k_batch_prefilter<0>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -289,7 +299,7 @@ cudaError_t batch_prepare(int form, int grad, int block, int minb) {
   e = cudaFuncSetAttribute(k_batch_prefilter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
-  void* k = select_batch_kernel(form, grad, minb);
+  void* k = select_batch_kernel(form, grad, minb, cheb);
   if (!k) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)topo_smem_bytes(block));
@@ -322,9 +332,9 @@ cudaError_t batch_count_uncovered(const BatchSetupArgs& a, const int64_t* px_off
   return cudaGetLastError();
 }
 
-cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb,
+cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb, bool cheb,
                             int* max_teams) {
-  void* k = select_batch_kernel(form, grad, minb);
+  void* k = select_batch_kernel(form, grad, minb, cheb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -358,8 +368,8 @@ cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int mi
 }
 
 cudaError_t batch_launch_iterate(int form, int grad, const BatchArgs& b, int n_teams, int block,
-                                 int minb, cudaStream_t s) {
-  void* k = select_batch_kernel(form, grad, minb);
+                                 int minb, bool cheb, cudaStream_t s) {
+  void* k = select_batch_kernel(form, grad, minb, cheb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(int), s);

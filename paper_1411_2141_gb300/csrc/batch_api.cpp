@@ -44,6 +44,7 @@ struct mreg_batch {
   mreg_options opts{};
   double alpha = 0.0, tau = 0.0, lam = 0.0;
   int form = 0, grad = 0;
+  bool cheb = false;   // S1 solved by Chebyshev semi-iteration
   std::vector<PairInfo> info;
   int64_t n_px = 0, n_nodes = 0, n_tris = 0, n_edges = 0, n_nnz = 0;
   void* arena = nullptr;
@@ -51,6 +52,7 @@ struct mreg_batch {
   // packed arrays (device)
   float *Re = nullptr, *Te = nullptr, *cTe = nullptr;
   __nv_bfloat16* cTe16 = nullptr;
+  __half* cTeh = nullptr;
   int* pix = nullptr;
   float2* u = nullptr;
   float2* F = nullptr;
@@ -68,6 +70,8 @@ struct mreg_batch {
   int* d_queue = nullptr;
   int64_t* d_px_off = nullptr;
   int* d_counts = nullptr;
+  int2* op_tiles = nullptr;   // (pair, first node) of the operator's blocks, on first use
+  int n_op_tiles = 0;
   // launch shape and its scratch
   int team_ctas = 2, block = 256, minb = 1, n_teams = 0;
   float* part = nullptr;     // per team reduction records
@@ -86,8 +90,8 @@ namespace {
 
 mreg_status choose_shape(mreg_batch* b, int ctas, int block, int minb) {
   int max_teams = 0;
-  CK(mreg::batch_prepare(b->form, b->grad, block, minb), "kernel attributes");
-  cudaError_t e = mreg::batch_max_teams(b->form, b->grad, ctas, block, minb, &max_teams);
+  CK(mreg::batch_prepare(b->form, b->grad, block, minb, b->cheb), "kernel attributes");
+  cudaError_t e = mreg::batch_max_teams(b->form, b->grad, ctas, block, minb, b->cheb, &max_teams);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(MREG_ERR_INVALID_ARG, "team shape %d x %d threads is not supported (%s)", ctas,
@@ -144,6 +148,7 @@ mreg_status enqueue_run(mreg_batch* b, int n_iters, cudaStream_t s) {
   CK(cudaMemsetAsync(b->last, 0, 8 * sizeof(double) * b->n_pairs, s), "memset stats");
   CK(mreg::batch_setup(b->setup, b->form == mreg::kFormFemEdges, s), "batched set-up");
   if (b->cTe16) CK(mreg::launch_to_bf16(b->cTe, b->n_px, b->cTe16, s), "BF16 coefficients");
+  if (b->cTeh) CK(mreg::launch_to_fp16(b->cTe, b->n_px, b->cTeh, s), "FP16 coefficients");
   CK(mreg::batch_pixel_map(b->setup, b->pix, b->n_px, s), "batched pixel map");
   mreg::BatchArgs a{};
   a.args = b->d_args;
@@ -157,7 +162,7 @@ mreg_status enqueue_run(mreg_batch* b, int n_iters, cudaStream_t s) {
   a.epart = b->epart;
   // external records: event nodes of the graph, readable after a replay
   CK(cudaEventRecordWithFlags(b->ev_iter[0], s, cudaEventRecordExternal), "event");
-  CK(mreg::batch_launch_iterate(b->form, b->grad, a, b->n_teams, b->block, b->minb, s),
+  CK(mreg::batch_launch_iterate(b->form, b->grad, a, b->n_teams, b->block, b->minb, b->cheb, s),
      "batched iteration kernel launch");
   CK(cudaEventRecordWithFlags(b->ev_iter[1], s, cudaEventRecordExternal), "event");
   CK(mreg::batch_warp_msd(b->warp, s), "batched warp");
@@ -219,6 +224,34 @@ mreg_status upload_image(mreg_batch* b, const mreg_image* im, float* dst, cudaSt
 
 extern "C" {
 
+mreg_status mreg_batch_apply_operator(mreg_batch* b, const float* x_dev, float* y_dev,
+                                      void* stream) {
+  if (!b || !x_dev || !y_dev) return fail(MREG_ERR_INVALID_ARG, "batch, x or y is NULL");
+  if (b->form == mreg::kFormExplicit)
+    return fail(MREG_ERR_INVALID_ARG, "the explicit mode has no system matrix");
+  if (x_dev == y_dev) return fail(MREG_ERR_INVALID_ARG, "x and y must not be the same buffer");
+  CK(cudaSetDevice(b->dev), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!b->op_tiles) {   // blocks of consecutive nodes, none straddling two pairs
+    const int per = mreg::operator_tile_nodes();
+    std::vector<int2> tiles;
+    for (int p = 0; p < b->n_pairs; ++p)
+      for (int i0 = 0; i0 < b->info[p].nV; i0 += per) tiles.push_back(make_int2(p, i0));
+    void* mem = nullptr;
+    const mreg_status st = b->mem.get(&mem, tiles.size() * sizeof(int2), stream);
+    if (st) return st;
+    CK(cudaMemcpyAsync(mem, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s),
+       "upload");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    b->op_tiles = (int2*)mem;
+    b->n_op_tiles = (int)tiles.size();
+  }
+  CK(mreg::launch_batch_apply_operator(b->form, b->d_args, b->setup.node_off, b->op_tiles,
+                                       b->n_op_tiles, (const float2*)x_dev, (float2*)y_dev, s),
+     "operator kernel launch");
+  return MREG_OK;
+}
+
 void mreg_batch_destroy(mreg_batch* b) {
   if (!b) return;
   cudaSetDevice(b->dev);
@@ -228,6 +261,7 @@ void mreg_batch_destroy(mreg_batch* b) {
     if (e) cudaEventDestroy(e);
   b->mem.put(b->part, nullptr);
   b->mem.put(b->epart, nullptr);
+  b->mem.put(b->op_tiles, nullptr);
   b->mem.put(b->arena, nullptr);
   delete b;
 }
@@ -325,6 +359,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   b->tau = tau;
   b->lam = lam;
   b->grad = o.grad;
+  b->cheb = use_chebyshev(o);
   b->form = o.mode == MREG_MODE_EXPLICIT ? mreg::kFormExplicit
             : o.mode == MREG_MODE_UMBRELLA_IMPLICIT
                 ? mreg::kFormUmbrella
@@ -383,7 +418,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   };
   const size_t o_Re = take(NP * 4), o_Te = take(NP * 4), o_tR = take(NP * 4), o_tT = take(NP * 4),
                o_cRe = take(NP * 4), o_cTe = take(NP * 4), o_pix = take(NP * 4),
-               o_c16 = take(o.coeff_bf16 ? NP * 2 : 0);
+               o_c16 = take(o.coeff_storage != MREG_COEFF_FP32 ? NP * 2 : 0);
   const size_t o_V = take(NN * 8), o_ReV = take(NN * 4), o_f = take(NN * 4), o_u = take(NN * 8),
                o_rt = take(NN * 8), o_dinv = take(NN * 4), o_lump = take(NN * 4),
                o_Md = take(NN * 4), o_Ad = take(NN * 4), o_F = take(2 * NN * 8),
@@ -414,7 +449,8 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   b->Re = F32(o_Re);
   b->Te = F32(o_Te);
   b->cTe = F32(o_cTe);
-  b->cTe16 = o.coeff_bf16 ? (__nv_bfloat16*)(base + o_c16) : nullptr;
+  b->cTe16 = o.coeff_storage == MREG_COEFF_BF16 ? (__nv_bfloat16*)(base + o_c16) : nullptr;
+  b->cTeh = o.coeff_storage == MREG_COEFF_FP16 ? (__half*)(base + o_c16) : nullptr;
   b->pix = I32(o_pix);
   b->u = (float2*)(base + o_u);
   b->F = (float2*)(base + o_F);
@@ -448,6 +484,16 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
     a.lam = (float)lam;
     a.area_floor = I.area_floor;
     a.rtol2 = (float)(o.pcg_rtol * o.pcg_rtol);
+    if (b->cheb) {
+      int m_min = 1, m_max = 1;
+      valence_range(hm[p].adj_ptr.data(), I.nV, &m_min, &m_max);
+      float cp[4];
+      chebyshev_params(lam, m_min, m_max, cp);
+      a.cheb_theta = cp[0];
+      a.cheb_delta = cp[1];
+      a.cheb_acosh = cp[2];
+      a.cheb_scale = cp[3];
+    }
     a.tau_ff = make_float2((float)tau, (float)(tau - (double)(float)tau));
     a.lam_ff = make_float2((float)lam, (float)(lam - (double)(float)lam));
     a.V = (const float2*)(base + o_V) + I.node;
@@ -466,6 +512,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
     a.lumped = F32(o_lump) + I.node;
     a.cTe = F32(o_cTe) + I.px;
     a.cTe16 = b->cTe16 ? b->cTe16 + I.px : nullptr;
+    a.cTeh = b->cTeh ? b->cTeh + I.px : nullptr;
     a.ReV = F32(o_ReV) + I.node;
     a.ReQ = F32(o_ReQ) + I.edge;
     a.u = (float2*)(base + o_u) + I.node;
@@ -495,6 +542,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
     w.u = a.u;
     w.cTe = a.cTe;
     w.cTe16 = a.cTe16;
+    w.cTeh = a.cTeh;
     w.Re = F32(o_Re) + I.px;
     mreg::PairSetup& ps = setup[p];
     ps.Re = F32(o_Re) + I.px;
@@ -587,7 +635,7 @@ mreg_status mreg_batch_create(int32_t n_pairs, const mreg_mesh* meshes, const mr
   wa.msd = (double*)(base + o_msd);
 
   // coverage check of every pair's pixel map
-  CK(mreg::batch_prepare(b->form, b->grad, 256, 1), "kernel attributes");
+  CK(mreg::batch_prepare(b->form, b->grad, 256, 1, b->cheb), "kernel attributes");
   CK(mreg::batch_setup(sa, false, s), "batched set-up");
   CK(mreg::batch_pixel_map(sa, b->pix, b->n_px, s), "batched pixel map");
   CK(cudaMemsetAsync(b->d_counts, 0, P * 4, s), "memset");
@@ -723,7 +771,11 @@ mreg_status mreg_batch_get_field(mreg_batch* b, int32_t pair, int32_t field, voi
     case MREG_FIELD_ENERGY: src = a.energy_hist, count = hist, esize = 8; break;
     case MREG_FIELD_PCG_ITERS: src = a.pcg_it_hist, count = hist; break;
     case MREG_FIELD_PCG_RESID: src = a.pcg_res_hist, count = hist, esize = 8; break;
-    case MREG_FIELD_COEF_TE_BF16: src = a.cTe16, count = a.cTe16 ? npx : 0, esize = 2; break;
+    case MREG_FIELD_COEF_TE_16:
+      src = a.cTeh ? (const void*)a.cTeh : (const void*)a.cTe16;
+      count = (a.cTe16 || a.cTeh) ? npx : 0;
+      esize = 2;
+      break;
     default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
   }
   if (count_out) *count_out = count;

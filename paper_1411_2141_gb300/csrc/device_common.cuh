@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,11 +53,22 @@ __device__ __forceinline__ void cubic_d2weights(float t, float e[4]) {
   e[3] = t;
 }
 
-// Coefficient loads: FP32, or BF16 storage widened exactly to FP32 (all the
-// arithmetic stays FP32).
+// Coefficient loads: FP32, or BF16 / FP16 storage widened exactly to FP32
+// (all the arithmetic stays FP32).
 __device__ __forceinline__ float load_coef(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_coef(const __nv_bfloat16* p) {
   return __bfloat162float(__ldg(p));
+}
+__device__ __forceinline__ float load_coef(const __half* p) { return __half2float(__ldg(p)); }
+
+// Calls fn with the coefficient array of Te that the arguments a (with cTe,
+// cTe16, cTeh) designate: the FP16 or the BF16 copy when one is set, else
+// the FP32 image.
+template <class A, class Fn>
+__device__ __forceinline__ auto with_te_coef(const A& a, Fn&& fn) {
+  if (a.cTeh) return fn(a.cTeh);
+  if (a.cTe16) return fn(a.cTe16);
+  return fn(a.cTe);
 }
 
 // Spline value at the point (bx + ox, by + oy) of a dense W x H coefficient
@@ -169,11 +181,6 @@ __device__ __forceinline__ void split_coord(float x, int& base, float& frac) {
 
 // ----------------------------------------------------------- grid barrier
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -181,6 +188,19 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *(const volatile int*)p;
+}
+
+// Spin-wait loads have acquire semantics (measured on GB300: polling with
+// relaxed loads closed by one acquire fence made the grid barrier slower).
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -194,17 +214,12 @@ __device__ __forceinline__ uint64_t global_ns() {
 // wait is bounded (timeout_ns, kBarrierTimeoutNs = 2 s by default): on timeout the
 // block raises kStatusBarrierTimeout | kStatusAbort and every block leaves at
 // its next barrier.  Must be reached by all threads of all blocks.
-//
-// skip_epoch > 0 makes this block leave out its arrival at barrier number
-// skip_epoch (a test of the failure path: the other blocks' waits, and its
-// own, then run out and the launch ends with the status above).
 struct GridBarrier {
   unsigned long long* counter;
   int* status;
   unsigned long long nblocks;
   unsigned long long epoch;
   uint64_t timeout_ns;
-  unsigned long long skip_epoch;
 
   // Returns false (block-uniformly) when the kernel must stop.  The wait is a
   // bare acquire-load loop; the abort flag and the clock are looked at only
@@ -213,7 +228,7 @@ struct GridBarrier {
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
-      if (epoch != skip_epoch) red_release_add(counter, 1ull);
+      red_release_add(counter, 1ull);
       const unsigned long long target = epoch * nblocks;
       int flag = 0;
       if (ld_acquire_u64(counter) < target) {
@@ -237,6 +252,57 @@ struct GridBarrier {
     }
     __syncthreads();
     return *s_flag == 0;
+  }
+};
+
+// Neighbour synchronisation between grid phases whose only cross-block
+// reads are a node's 1-ring (no reduction): block b publishes the number of
+// the phase it has finished in flags[b] (release) and waits (acquire) until
+// each block that owns a neighbour of one of its nodes (nbr[0 .. n_nbr)) has
+// finished the same phase.  The data a phase writes are double-buffered by
+// the callers, and the neighbour relation is symmetric, so this also keeps a
+// block from overwriting values its neighbours still read.  Every wait is
+// bounded like the grid barrier's; a block that gives up raises
+// kStatusBarrierTimeout | kStatusAbort, and a block that sees the abort bit
+// leaves.  Returns false (block-uniformly) when the kernel must stop.
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct NeighbourSync {
+  unsigned* flags;     // one per block, zero at launch
+  const int* nbr;      // this block's neighbour blocks
+  int n_nbr, rank;
+  unsigned epoch;
+  uint64_t timeout_ns;
+  int* status;
+
+  __device__ __forceinline__ bool sync() {
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) st_release_u32(flags + rank, epoch);
+    int flag = 0;
+    if ((int)threadIdx.x < n_nbr) {
+      const unsigned* f = flags + __ldg(nbr + threadIdx.x);
+      if (ld_acquire_u32(f) < epoch) {
+        const uint64_t t0 = global_ns();
+        for (unsigned spin = 1;; ++spin) {
+          if (ld_acquire_u32(f) >= epoch) break;
+          if ((spin & 31u) == 0) {
+            if (ld_volatile_i32(status) & kStatusAbort) {
+              flag = 1;
+              break;
+            }
+            if (global_ns() - t0 > timeout_ns) {
+              atomicOr(status, kStatusBarrierTimeout | kStatusAbort);
+              flag = 1;
+              break;
+            }
+          }
+        }
+      }
+    }
+    return __syncthreads_or(flag) == 0;
   }
 };
 

@@ -46,6 +46,16 @@ mreg_status validate_image(const mreg_image* im, const char* name);
 // Option checks shared by every entry point that takes mreg_options;
 // *lam receives the smoothing weight.
 mreg_status validate_options(const mreg_options& o, double alpha, double tau, double* lam);
+// Whether the semi-implicit solve of mode uses Chebyshev semi-iteration.
+inline bool use_chebyshev(const mreg_options& o) {
+  return o.mode == MREG_MODE_UMBRELLA_IMPLICIT && o.solver != MREG_SOLVER_CG;
+}
+// The scalars of the S1 Chebyshev solve (IterArgs cheb_*) for smoothing
+// weight lam and node valences in [m_min, m_max]: out = {theta, delta,
+// acosh(theta / delta), sqrt(m_max / m_min) / safety}.
+void chebyshev_params(double lam, int m_min, int m_max, float out[4]);
+// Smallest and largest row length of a CSR row-pointer array.
+void valence_range(const int* ptr, int n, int* m_min, int* m_max);
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Device memory of one handle: the caller's allocator from mreg_options, or

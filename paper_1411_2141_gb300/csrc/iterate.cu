@@ -11,16 +11,45 @@ namespace mreg {
 namespace {
 
 // The team of the grid engine: every block of the cooperative launch.
+// sync_local() is for phases whose only cross-block reads are 1-ring values
+// (the Chebyshev steps): the neighbour synchronisation when the launch has
+// neighbour lists, else the grid barrier.  stall > 0 (a test of the failure
+// path) makes this block leave the kernel at its synchronisation number
+// stall, as a block that failed would: it neither arrives nor publishes, so
+// the other blocks' bounded waits run out and the launch ends with
+// kStatusBarrierTimeout | kStatusAbort.
 struct GridTeam {
   GridBarrier gb;
+  NeighbourSync ns;
   int* s_flag;
   int rank, nb;
-  __device__ __forceinline__ bool sync() { return gb.sync(s_flag); }
+  int n_sync, stall;
+  __device__ __forceinline__ bool sync() {
+    if (++n_sync == stall) return false;
+    return gb.sync(s_flag);
+  }
+  __device__ __forceinline__ bool sync_local() {
+    if (++n_sync == stall) return false;
+    return ns.flags ? ns.sync() : gb.sync(s_flag);
+  }
 };
 
+__device__ __forceinline__ NeighbourSync neighbour_sync(const IterArgs& a) {
+  NeighbourSync s{};
+  if (a.nflags) {
+    s.flags = a.nflags;
+    s.nbr = a.nbr_idx + (size_t)blockIdx.x * kMaxNbr;
+    s.n_nbr = __ldg(a.nbr_cnt + blockIdx.x);
+    s.rank = (int)blockIdx.x;
+    s.epoch = 0;
+    s.timeout_ns = a.barrier_timeout_ns;
+    s.status = a.status;
+  }
+  return s;
+}
+
 __device__ __forceinline__ GridBarrier grid_barrier(const IterArgs& a) {
-  return GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull, a.barrier_timeout_ns,
-                     (int)blockIdx.x == a.stall_block ? (unsigned long long)a.stall_barrier : 0ull};
+  return GridBarrier{a.bar, a.status, (unsigned long long)gridDim.x, 0ull, a.barrier_timeout_ns};
 }
 
 // A handle whose earlier launch gave up at a barrier keeps the abort bit
@@ -38,18 +67,26 @@ __global__ void __launch_bounds__(kIterBlockMax, MINB) k_explicit(const IterArgs
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
   if (aborted(a)) return;
-  GridTeam team{grid_barrier(a), &s_flag, (int)blockIdx.x, (int)gridDim.x};
+  GridTeam team{grid_barrier(a), neighbour_sync(a), &s_flag, (int)blockIdx.x, (int)gridDim.x, 0,
+                (int)blockIdx.x == a.stall_block ? a.stall_barrier : 0};
   run_explicit<GRAD>(a, team, dsm);
 }
 
-// L: lanes per node (1, or 2 with the neighbour lists split between them).
-template <int FORM, int GRAD, int MINB, int L>
+// L: lanes per node (1, or 2 with the neighbour lists split between them);
+// CHEB: the S1 solve by Chebyshev semi-iteration instead of CG.
+template <int FORM, int GRAD, int MINB, int L, bool CHEB>
 __global__ void __launch_bounds__(kIterBlockMax, MINB) k_implicit(const IterArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_flag;
   if (aborted(a)) return;
-  GridTeam team{grid_barrier(a), &s_flag, (int)blockIdx.x, (int)gridDim.x};
-  run_implicit<FORM, GRAD, L>(a, team, dsm);
+  GridTeam team{grid_barrier(a), neighbour_sync(a), &s_flag, (int)blockIdx.x, (int)gridDim.x, 0,
+                (int)blockIdx.x == a.stall_block ? a.stall_barrier : 0};
+  if constexpr (CHEB) {
+    static_assert(FORM == kFormUmbrella, "the Chebyshev solve is the S1 form's");
+    run_chebyshev<GRAD, L>(a, team, dsm);
+  } else {
+    run_implicit<FORM, GRAD, L>(a, team, dsm);
+  }
 }
 
 // The two terms of Eq. 1 at the current u (a report, not on the iteration
@@ -112,8 +149,9 @@ __global__ void __launch_bounds__(kTermsBlock) k_energy_terms(const IterArgs a, 
       split_coord(va.y, by, fy);
       const float ox = fx + 0.5f * ((vb.x - va.x) + (ua.x + ub.x));
       const float oy = fy + 0.5f * ((vb.y - va.y) + (ua.y + ub.y));
-      const float fq = a.cTe16 ? spline_sample<false>(a.cTe16, a.W, a.H, bx, by, ox, oy, &gx, &gy)
-                               : spline_sample<false>(a.cTe, a.W, a.H, bx, by, ox, oy, &gx, &gy);
+      const float fq = with_te_coef(a, [&](const auto* c) {
+        return spline_sample<false>(c, a.W, a.H, bx, by, ox, oy, &gx, &gy);
+      });
       const double r = (double)fq - __ldg(a.ReQ + q);
       d += 0.5 * (double)__ldg(a.edge_w + q) * r * r;
     }
@@ -164,27 +202,75 @@ __global__ void k_energy_final(const float2* __restrict__ epart, int ewarps, int
   }
 }
 
+// Neighbour blocks of block b: the blocks that own a 1-ring neighbour of a
+// node that b owns (node i belongs to node slot i mod nnth, and slot s to
+// block s / npb, npb = nodes per block and round), as a bit set in shared
+// memory, then listed in ascending order.
+__global__ void k_neighbour_blocks(const int* __restrict__ adj_ptr, const int* __restrict__ adj_col,
+                                   int nV, int nnth, int npb, int grid, int* __restrict__ nbr_idx,
+                                   int* __restrict__ nbr_cnt) {
+  extern __shared__ unsigned bits[];
+  const int b = blockIdx.x, words = (grid + 31) / 32;
+  for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+  __syncthreads();
+  for (int so = threadIdx.x; so < npb; so += blockDim.x) {
+    for (int i = b * npb + so; i < nV; i += nnth) {
+      for (int k = __ldg(adj_ptr + i); k < __ldg(adj_ptr + i + 1); ++k) {
+        const int ob = (__ldg(adj_col + k) % nnth) / npb;
+        if (ob != b) atomicOr(bits + (ob >> 5), 1u << (ob & 31));
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int w = 0; w < words; ++w) {
+      for (unsigned m = bits[w]; m; m &= m - 1u) {
+        if (n < kMaxNbr) nbr_idx[(size_t)b * kMaxNbr + n] = 32 * w + __ffs(m) - 1;
+        ++n;
+      }
+    }
+    nbr_cnt[b] = n;
+  }
+}
+
 template <int MINB, int L>
-void* select_kernel_m(int form, int grad) {
+void* select_kernel_m(int form, int grad, bool cheb) {
+  if (cheb) {
+    if (form != kFormUmbrella) return nullptr;
+    return grad ? (void*)k_implicit<kFormUmbrella, 1, MINB, L, true>
+                : (void*)k_implicit<kFormUmbrella, 0, MINB, L, true>;
+  }
   switch (form * 2 + (grad ? 1 : 0)) {
     case 0: return L == 1 ? (void*)k_explicit<0, MINB> : nullptr;
     case 1: return L == 1 ? (void*)k_explicit<1, MINB> : nullptr;
-    case 2: return (void*)k_implicit<kFormUmbrella, 0, MINB, L>;
-    case 3: return (void*)k_implicit<kFormUmbrella, 1, MINB, L>;
-    case 4: return (void*)k_implicit<kFormFemNodes, 0, MINB, L>;
-    case 5: return (void*)k_implicit<kFormFemNodes, 1, MINB, L>;
-    case 7: return (void*)k_implicit<kFormFemEdges, 1, MINB, L>;
+    case 2: return (void*)k_implicit<kFormUmbrella, 0, MINB, L, false>;
+    case 3: return (void*)k_implicit<kFormUmbrella, 1, MINB, L, false>;
+    case 4: return (void*)k_implicit<kFormFemNodes, 0, MINB, L, false>;
+    case 5: return (void*)k_implicit<kFormFemNodes, 1, MINB, L, false>;
+    case 7: return (void*)k_implicit<kFormFemEdges, 1, MINB, L, false>;
     default: return nullptr;
   }
 }
 
 // Two lanes per node only with the full register budget (one block per SM).
-void* select_kernel(int form, int grad, int minb, int lanes) {
-  if (lanes == 2) return minb == 1 ? select_kernel_m<1, 2>(form, grad) : nullptr;
-  return minb == 2 ? select_kernel_m<2, 1>(form, grad) : select_kernel_m<1, 1>(form, grad);
+void* select_kernel(int form, int grad, int minb, int lanes, bool cheb) {
+  if (lanes == 2) return minb == 1 ? select_kernel_m<1, 2>(form, grad, cheb) : nullptr;
+  return minb == 2 ? select_kernel_m<2, 1>(form, grad, cheb)
+                   : select_kernel_m<1, 1>(form, grad, cheb);
 }
 
 }  // namespace
+
+cudaError_t launch_neighbour_blocks(const int* adj_ptr, const int* adj_col, int nV, int grid,
+                                    int block, int lanes, int* nbr_idx, int* nbr_cnt,
+                                    cudaStream_t s) {
+  const int npb = block / lanes;
+  const size_t smem = sizeof(unsigned) * (size_t)((grid + 31) / 32);
+  k_neighbour_blocks<<<grid, 256, smem, s>>>(adj_ptr, adj_col, nV, npb * grid, npb, grid, nbr_idx,
+                                             nbr_cnt);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* part, double* out,
                                 cudaStream_t s) {
@@ -193,9 +279,9 @@ cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* p
   return cudaGetLastError();
 }
 
-cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes,
+cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes, bool cheb,
                                int* max_blocks_per_sm) {
-  void* k = select_kernel(form, grad, minb, lanes);
+  void* k = select_kernel(form, grad, minb, lanes, cheb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -203,15 +289,19 @@ cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lane
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k, block, smem);
 }
 
-cudaError_t launch_iterate(int form, int grad, int minb, int lanes, const IterArgs& a, int grid,
-                           int block, cudaStream_t s) {
-  void* k = select_kernel(form, grad, minb, lanes);
+cudaError_t launch_iterate(int form, int grad, int minb, int lanes, bool cheb, const IterArgs& a,
+                           int grid, int block, cudaStream_t s) {
+  void* k = select_kernel(form, grad, minb, lanes, cheb);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = topo_smem_bytes(block);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if (a.nflags) {
+    e = cudaMemsetAsync(a.nflags, 0, sizeof(unsigned) * grid, s);
+    if (e != cudaSuccess) return e;
+  }
   IterArgs copy = a;
   void* args[] = {(void*)&copy};
   e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), args, smem, s);

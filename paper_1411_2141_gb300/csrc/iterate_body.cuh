@@ -771,6 +771,385 @@ __device__ __forceinline__ bool run_implicit(const IterArgs& a, TEAM& team, unsi
   return true;
 }
 
+// ======================================================================
+// S1: semi-implicit step solved by Chebyshev semi-iteration
+// ======================================================================
+// The S1 matrix A = (1+l) D_m - l W has the Jacobi-scaled form
+//   D^-1 A = I - l/(1+l) D_m^-1 W,   D = diag(A) = (1+l) D_m,
+// and D_m^-1 W (a random-walk matrix, similar to the symmetric
+// D_m^-1/2 W D_m^-1/2) has its spectrum in [-1, 1]; so the spectrum of
+// D^-1 A lies in [1/(1+l), (1+2l)/(1+l)], known in closed form (the host
+// passes it as cheb_theta +- cheb_delta, slightly widened).  Chebyshev
+// semi-iteration on that interval (Golub and Varga, Numer. Math. 3, 1961;
+// Saad, "Iterative Methods for Sparse Linear Systems", Sec. 12.3) needs no
+// inner products.  Each step is one team phase with a barrier and no
+// reduction:
+//   r_j = b - A x_j                         (float-float, then FP32)
+//   d_0 = D^-1 r_0 / theta,  d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) D^-1 r_j
+//   x_{j+1} = x_j + d_j,     rho_0 = delta / theta,  rho_j = 1 / (2 theta / delta - rho_{j-1}).
+// The residual is formed from b and A x_j at every step, so rounding does
+// not accumulate in a recursion.  In exact arithmetic
+//   ||r_k||_2 <= sqrt(max diag A / min diag A) ||r_0||_2 / T_k(theta / delta)
+// (T_k the Chebyshev polynomial of the first kind), so the step count k of a
+// solve follows from ||r_0|| / ||b||: the one reduction of a solve, taken
+// with the right-hand side in the solve's first phase.  The solve is then
+// verified: the true residual of its final iterate is formed in float-float
+// in the first phase of the next iteration (which forms A x of the same
+// iterate for its own right-hand side) or, for a launch's last solve, in a
+// phase of its own.  A solve that misses rtol is continued from its iterate
+// (the recurrence restarted, the right-hand side kept) and verified again,
+// up to the step cap.
+//
+// Phases of one iteration: [sample at the launch start] -> B (force, the
+// previous solve's residual, b, r_0, the first step; one reduction) ->
+// steps 1 .. k-1, the last one sampling Te at the final iterate for the
+// next iteration.  The state lives in the CG arrays' memory: b in two
+// buffers (the pending solve's and the current one's), x in two (parity),
+// d in one.
+
+// Scalars of one Chebyshev step: d' = c_d d + c_r D^-1 r.
+struct ChebStep {
+  float c_d, c_r;
+};
+
+// The rho recurrence (the same in every thread: IEEE operations on the
+// same values).
+struct ChebSeq {
+  float sigma, rho;
+  __device__ __forceinline__ static ChebSeq start(const IterArgs& a) {
+    ChebSeq s;
+    s.sigma = a.cheb_theta / a.cheb_delta;
+    s.rho = a.cheb_delta / a.cheb_theta;   // rho_0
+    return s;
+  }
+  __device__ __forceinline__ ChebStep first(const IterArgs& a) const {
+    return ChebStep{0.0f, 1.0f / a.cheb_theta};
+  }
+  __device__ __forceinline__ ChebStep next(const IterArgs& a) {
+    const float rn = 1.0f / (2.0f * sigma - rho);
+    const ChebStep s{rn * rho, 2.0f * rn / a.cheb_delta};
+    rho = rn;
+    return s;
+  }
+};
+
+// Steps k such that the bound above brings max_c ||r_c|| / ||b_c|| below
+// rtol, from the current r2 = ||r||^2 and b2 = ||b||^2 of both components;
+// at least 1, at most maxit (also for a non-finite residual, or b = 0 with
+// a non-zero residual).
+__device__ __forceinline__ int cheb_steps_needed(const IterArgs& a, const float r2[2],
+                                                 const float b2[2]) {
+  int k = 1;
+  for (int c = 0; c < 2; ++c) {
+    if (!(r2[c] <= 3.0e38f)) return a.maxit;   // NaN or Inf
+    if (r2[c] == 0.0f) continue;
+    if (!(b2[c] > 0.0f)) return a.maxit;
+    const float Q = a.cheb_scale * sqrtf(r2[c] / (a.rtol2 * b2[c]));
+    if (Q > 1.0f) k = max(k, (int)ceilf(acoshf(Q) / a.cheb_acosh));
+  }
+  return min(k, a.maxit);
+}
+
+// (A x)_i of S1 in float-float: the node's lanes split its neighbours.
+template <int L>
+__device__ __forceinline__ AxAcc<kFormUmbrella> cheb_ax(const IterArgs& a, const Topo& T,
+                                                        bool cached, const float2* x, int i,
+                                                        float2 xi, int& deg,
+                                                        const NodeLanes<L>& nl) {
+  int beg;
+  T.arow(a, cached, i, beg, deg);
+  AxAcc<kFormUmbrella> A;
+  A.init_part(a, i, xi, nl.lead());
+  for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
+    float2 xj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      xj[u] = (k0 + u < deg) ? x[T.adj(a, cached, beg, k0 + u)] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u < deg) A.add(a, beg + k0 + u, xj[u]);
+  }
+  nl.sum(A);
+  A.finish(a, deg, xi);
+  return A;
+}
+
+__device__ __forceinline__ float2 ff_residual(float4 b4, const AxAcc<kFormUmbrella>& A) {
+  return make_float2(ff_to_f(ff_add(ff{b4.x, b4.y}, ff_neg(A.ax))),
+                     ff_to_f(ff_add(ff{b4.z, b4.w}, ff_neg(A.ay))));
+}
+
+// Phase B at node i: the force (mesh gradient of the neighbours' samples;
+// with the spline gradient it was formed with the sample), the residual of
+// the pending solve's iterate against its right-hand side bprev (when one
+// is pending), b = D_m (x - tau F), r_0 = b - A x and the first step.
+// acc: ||r_prev||^2 (x, y), ||b||^2 (x, y), ||r_0||^2 (x, y).
+template <int GRAD, int L>
+__device__ __forceinline__ void cheb_start_node(const IterArgs& a, const Topo& T, bool cached,
+                                                const float2* x, float2* xn, float2* dd,
+                                                const float4* bprev, float4* bnew, float2* F,
+                                                int i, float* acc, const NodeLanes<L>& nl) {
+  const float2 xi = x[i];
+  float2 Fi;
+  if (GRAD == 1) {
+    Fi = F[i];
+  } else {
+    Fi = neighbour_force_c<kFormUmbrella, L>(a, T, cached, DispPlain{x}, FPlain{a.f}, i, xi,
+                                             a.f[i], nl);
+    if (nl.lead()) F[i] = Fi;
+  }
+  int deg;
+  const AxAcc<kFormUmbrella> A = cheb_ax<L>(a, T, cached, x, i, xi, deg, nl);
+  if (!nl.lead()) return;
+  if (bprev) {
+    const float2 rv = ff_residual(bprev[i], A);
+    acc[0] += rv.x * rv.x;
+    acc[1] += rv.y * rv.y;
+  }
+  const ff tau = ff_load(a.tau_ff);
+  const ff bx = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.x)), xi.x), (float)deg);
+  const ff by = ff_mul_f(ff_add_f(ff_neg(ff_mul_f(tau, Fi.y)), xi.y), (float)deg);
+  const float4 b4 = make_float4(bx.hi, bx.lo, by.hi, by.lo);
+  bnew[i] = b4;
+  const float2 r = ff_residual(b4, A);
+  const float bxf = ff_to_f(bx), byf = ff_to_f(by);
+  acc[2] += bxf * bxf;
+  acc[3] += byf * byf;
+  acc[4] += r.x * r.x;
+  acc[5] += r.y * r.y;
+  const float c = __ldg(a.dinv + i) / a.cheb_theta;
+  const float2 d = make_float2(c * r.x, c * r.y);
+  dd[i] = d;
+  xn[i] = make_float2(xi.x + d.x, xi.y + d.y);
+}
+
+// One step at node i (x -> xn); with SAMPLE also Te at the new iterate:
+// f, the energy term into e and (spline gradient) the force into Fs.
+template <int GRAD, int L, bool SAMPLE>
+__device__ __forceinline__ void cheb_step_node(const IterArgs& a, const Topo& T, bool cached,
+                                               const float2* x, float2* xn, float2* dd,
+                                               const float4* b, int i, ChebStep s, bool first,
+                                               float2* Fs, ff& e, const NodeLanes<L>& nl) {
+  const float2 xi = x[i];
+  int deg;
+  const AxAcc<kFormUmbrella> A = cheb_ax<L>(a, T, cached, x, i, xi, deg, nl);
+  if (!nl.lead()) return;
+  const float2 r = ff_residual(b[i], A);
+  const float di = __ldg(a.dinv + i);
+  float2 d = make_float2(s.c_r * (di * r.x), s.c_r * (di * r.y));
+  if (!first) {
+    const float2 dp = dd[i];
+    d = make_float2(__fmaf_rn(s.c_d, dp.x, d.x), __fmaf_rn(s.c_d, dp.y, d.y));
+  }
+  dd[i] = d;
+  const float2 x1 = make_float2(xi.x + d.x, xi.y + d.y);
+  xn[i] = x1;
+  if (SAMPLE) {
+    float2 unusedF;
+    e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, i, x1, a.f + i, Fs + i, &unusedF));
+  }
+}
+
+// Residual of the iterate x against b at node i: acc += ||b - A x||^2 (x, y).
+template <int L>
+__device__ __forceinline__ void cheb_verify_node(const IterArgs& a, const Topo& T, bool cached,
+                                                 const float2* x, const float4* b, int i,
+                                                 float* acc, const NodeLanes<L>& nl) {
+  int deg;
+  const AxAcc<kFormUmbrella> A = cheb_ax<L>(a, T, cached, x, i, x[i], deg, nl);
+  if (!nl.lead()) return;
+  const float2 rv = ff_residual(b[i], A);
+  acc[0] += rv.x * rv.x;
+  acc[1] += rv.y * rv.y;
+}
+
+// The record of a verified solve (one thread of the team).
+__device__ __forceinline__ void cheb_record(const IterArgs& a, int it, int steps, const float r2[2],
+                                            const float b2[2], bool capped) {
+  double rel = 0.0;
+  for (int c = 0; c < 2; ++c) {
+    const double qq = b2[c] > 0.0f ? sqrt((double)r2[c] / (double)b2[c]) : (r2[c] > 0.0f ? 1.0 : 0.0);
+    rel = qq > rel ? qq : rel;
+  }
+  const int hi = a.it0 + it;
+  if (hi < a.hist_cap) {
+    a.pcg_it_hist[hi] = steps;
+    a.pcg_res_hist[hi] = rel;
+  }
+  a.last[1] = rel;
+  a.last[2] = (double)steps;
+  if ((double)steps > a.last[3]) a.last[3] = (double)steps;
+  if (capped) {
+    a.last[4] += 1.0;
+    atomicOr(a.status, kStatusNotConverged);
+  }
+}
+
+// n Chebyshev steps from the iterate in xc against b (xc and xn swap after
+// each step, so that xc holds the current iterate).  A step reads 1-ring
+// values only, so the steps are separated by the team's local
+// synchronisation;
+// first: the first step starts the recurrence (d = D^-1 r / theta), else the
+// steps continue a recurrence whose step 0 was taken in phase B.  The last
+// step samples Te at the final iterate (F into Fs with the spline gradient,
+// the energy into the slot eslot); n = 0 is a phase that only samples.
+template <int GRAD, int L, class TEAM>
+__device__ __forceinline__ bool cheb_steps(const IterArgs& a, TEAM& team, const Topo& T,
+                                           const NodeLanes<L>& nl, float2*& xc, float2*& xn,
+                                           float2* dd, const float4* b, int n, bool first,
+                                           float2* Fs, float2* eslot, int ntid, int nnth,
+                                           int gwarp) {
+  const int nV = a.nV;
+  if (n == 0) {
+    ff e = ff_zero();
+    FOR_NODES(i, cached) {
+      (void)cached;
+      if (!nl.lead()) continue;
+      float2 unusedF;
+      e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, i, xc[i], a.f + i, Fs + i, &unusedF));
+    }
+    warp_energy_store(e, eslot, gwarp);
+    return team.sync_local();
+  }
+  ChebSeq seq = ChebSeq::start(a);
+  for (int j = 0; j < n; ++j) {
+    const bool f0 = first && j == 0;
+    const ChebStep s = f0 ? seq.first(a) : seq.next(a);
+    ff e = ff_zero();
+    if (j + 1 < n) {
+      FOR_NODES(i, cached) cheb_step_node<GRAD, L, false>(a, T, cached, xc, xn, dd, b, i, s, f0, Fs, e, nl);
+    } else {
+      FOR_NODES(i, cached) cheb_step_node<GRAD, L, true>(a, T, cached, xc, xn, dd, b, i, s, f0, Fs, e, nl);
+      warp_energy_store(e, eslot, gwarp);
+    }
+    if (!team.sync_local()) return false;
+    float2* t = xc;
+    xc = xn;
+    xn = t;
+  }
+  return true;
+}
+
+template <int GRAD, int L, class TEAM>
+__device__ __forceinline__ bool run_chebyshev(const IterArgs& a, TEAM& team, unsigned char* dsm) {
+  __shared__ float s_red[kMaxWarps * kRec];
+  __shared__ float s_tot[2 * kRec];
+  const int tid = team.rank * blockDim.x + threadIdx.x;
+  const int nth = team.nb * blockDim.x;
+  const int nb = team.nb;
+  const bool lead = team.rank == 0 && threadIdx.x == 0;
+  const int nV = a.nV;
+  const int bd = blockDim.x;
+  const int gwarp = tid >> 5;   // energy partials are kept per warp
+  const int ntid = tid / L, nnth = nth / L;   // node slots
+  const NodeLanes<L> nl = NodeLanes<L>::make();
+  Topo T{(int*)dsm, (float*)(dsm + (size_t)kCacheA * bd * sizeof(int)),
+         (int2*)(dsm + (size_t)kCacheA * bd * (sizeof(int) + sizeof(float))), bd, (int)threadIdx.x};
+  if (ntid < nV) T.fill(a, ntid);
+  // b of solves of even and odd iterations; the iterate (xc) and the next
+  // one (xn), swapped by pointer; d
+  float4* const bb0 = a.cg;
+  float4* const bb1 = a.cg + nV;
+  float2* xc = reinterpret_cast<float2*>(a.cg + 2 * (size_t)nV);
+  float2* xn = xc + nV;
+  float2* const dd = xc + 2 * (size_t)nV;
+  int par = 0;   // half of the partial-sum buffer used by the next reduction
+
+  for (int i = tid; i < nV; i += nth) xc[i] = a.u[i];
+  SYNC_OR_LEAVE();
+  {  // sample at the initial iterate (energy of the launch's iteration 0)
+    ff e = ff_zero();
+    FOR_NODES(i, cached) {
+      (void)cached;
+      if (!nl.lead()) continue;
+      float2 unusedF;
+      e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, i, xc[i], a.f + i, a.F + i, &unusedF));
+    }
+    warp_energy_store(e, a.epart, gwarp);
+    SYNC_OR_LEAVE();
+  }
+
+  int pend_it = -1, pend_steps = 0;   // the solve awaiting verification
+  float pend_b2[2] = {0.0f, 0.0f};
+  for (int it = 0; it < a.n_iters; ++it) {
+    float2* F = a.F + (size_t)(it & 1) * nV;
+    float2* Fn = a.F + (size_t)((it + 1) & 1) * nV;
+    float tot[6];
+    for (;;) {
+      // ---- B: force, the pending solve's residual, b, r_0, step 0 -------
+      float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      const float4* bprev = pend_it < 0 ? nullptr : ((pend_it & 1) ? bb1 : bb0);
+      float4* const bcur = (it & 1) ? bb1 : bb0;
+      FOR_NODES(i, cached) cheb_start_node<GRAD, L>(a, T, cached, xc, xn, dd, bprev, bcur, F, i, acc, nl);
+      block_record<6, false>(acc, ff_zero(), MY_REC, s_red);
+      SYNC_OR_LEAVE();
+      ff unused;
+      grid_totals<6, false>(ALL_REC, nb, tot, unused, s_tot + par * kRec);
+      par ^= 1;
+      if (pend_it >= 0) {
+        const float rv2[2] = {tot[0], tot[1]};
+        const bool ok = rv2[0] <= a.rtol2 * pend_b2[0] && rv2[1] <= a.rtol2 * pend_b2[1];
+        if (!ok && pend_steps < a.maxit) {
+          // continue the pending solve from its iterate (still xc: phase B
+          // wrote only xn), then redo phase B
+          const int n = min(cheb_steps_needed(a, rv2, pend_b2), a.maxit - pend_steps);
+          if (!cheb_steps<GRAD, L>(a, team, T, nl, xc, xn, dd, bprev, n, true, F,
+                                   a.epart + (size_t)it * a.ewarps, ntid, nnth, gwarp))
+            return false;
+          pend_steps += n;
+          continue;
+        }
+        if (lead) cheb_record(a, pend_it, pend_steps, rv2, pend_b2, !ok);
+      }
+      break;
+    }
+    {   // x_1 of this solve becomes the iterate
+      float2* t = xc;
+      xc = xn;
+      xn = t;
+    }
+    const float b2[2] = {tot[2], tot[3]}, r02[2] = {tot[4], tot[5]};
+    // steps 1 .. k-1 (the last one samples the final iterate; with a cap of
+    // one step, a phase samples x_1)
+    const int k = min(max(2, cheb_steps_needed(a, r02, b2)), a.maxit);
+    if (!cheb_steps<GRAD, L>(a, team, T, nl, xc, xn, dd, (it & 1) ? bb1 : bb0, k - 1, false, Fn,
+                             a.epart + (size_t)(it + 1) * a.ewarps, ntid, nnth, gwarp))
+      return false;
+    pend_it = it;
+    pend_steps = k;
+    pend_b2[0] = b2[0];
+    pend_b2[1] = b2[1];
+  }
+
+  // ---- verify the launch's last solve -------------------------------------
+  while (pend_it >= 0) {
+    float acc[2] = {0.0f, 0.0f};
+    const float4* bprev = (pend_it & 1) ? bb1 : bb0;
+    FOR_NODES(i, cached) cheb_verify_node<L>(a, T, cached, xc, bprev, i, acc, nl);
+    block_record<2, false>(acc, ff_zero(), MY_REC, s_red);
+    SYNC_OR_LEAVE();
+    ff unused;
+    float rv2[2];
+    grid_totals<2, false>(ALL_REC, nb, rv2, unused, s_tot + par * kRec);
+    par ^= 1;
+    const bool ok = rv2[0] <= a.rtol2 * pend_b2[0] && rv2[1] <= a.rtol2 * pend_b2[1];
+    if (!ok && pend_steps < a.maxit) {
+      const int n = min(cheb_steps_needed(a, rv2, pend_b2), a.maxit - pend_steps);
+      if (!cheb_steps<GRAD, L>(a, team, T, nl, xc, xn, dd, bprev, n, true,
+                               a.F + (size_t)(a.n_iters & 1) * nV,
+                               a.epart + (size_t)a.n_iters * a.ewarps, ntid, nnth, gwarp))
+        return false;
+      pend_steps += n;
+      continue;
+    }
+    if (lead) cheb_record(a, pend_it, pend_steps, rv2, pend_b2, !ok);
+    pend_it = -1;
+  }
+  // hand the displacement back in u (every node's final x is written)
+  for (int i = tid; i < nV; i += nth) a.u[i] = xc[i];
+  return true;
+}
+
 #undef MY_REC
 #undef ALL_REC
 #undef SYNC_OR_LEAVE

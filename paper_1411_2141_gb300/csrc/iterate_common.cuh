@@ -16,8 +16,9 @@ __device__ __forceinline__ float sample_at_node(const IterArgs& a, float2 v, flo
   float fx, fy;
   split_coord(v.x, bx, fx);
   split_coord(v.y, by, fy);
-  if (a.cTe16) return spline_sample<GRAD>(a.cTe16, a.W, a.H, bx, by, fx + u.x, fy + u.y, gx, gy);
-  return spline_sample<GRAD>(a.cTe, a.W, a.H, bx, by, fx + u.x, fy + u.y, gx, gy);
+  return with_te_coef(a, [&](const auto* c) {
+    return spline_sample<GRAD>(c, a.W, a.H, bx, by, fx + u.x, fy + u.y, gx, gy);
+  });
 }
 
 // Displacement readers: the explicit kernel keeps u in a.u, the implicit
@@ -117,8 +118,9 @@ __device__ __forceinline__ float sample_edge(const IterArgs& a, int q, int2 ab, 
   const float ox = fx + 0.5f * ((vb.x - va.x) + (ua.x + ub.x));
   const float oy = fy + 0.5f * ((vb.y - va.y) + (ua.y + ub.y));
   float gx, gy;
-  const float fq = a.cTe16 ? spline_sample<true>(a.cTe16, a.W, a.H, bx, by, ox, oy, &gx, &gy)
-                           : spline_sample<true>(a.cTe, a.W, a.H, bx, by, ox, oy, &gx, &gy);
+  const float fq = with_te_coef(a, [&](const auto* c) {
+    return spline_sample<true>(c, a.W, a.H, bx, by, ox, oy, &gx, &gy);
+  });
   const float rq = fq - __ldg(a.ReQ + q);
   const float w = __ldg(a.edge_w + q);
   const float h = 0.5f * w * rq;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +21,10 @@ constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s
 // grid barrier), and the largest number of warps per block.
 constexpr int kRec = 12;
 constexpr int kMaxWarps = 32;
+// Most neighbour blocks a block of the grid engine may wait on in the
+// neighbour synchronisation (one polling thread each; blocks have >= 32
+// threads); launch shapes with more use the grid barrier throughout.
+constexpr int kMaxNbr = 32;
 
 // Update / solve forms of the iteration kernel.
 enum Form : int {
@@ -34,6 +39,10 @@ struct IterArgs {
   int nV, nE, W, H, n_iters, it0, maxit, hist_cap;   // it0: history index of iteration 0
   int smooth_passes;     // S0: Eq. 14 passes per iteration (>= 1)
   float tau, lam, area_floor, rtol2;
+  // S1 by Chebyshev semi-iteration: centre and half-width of an interval
+  // holding the spectrum of D^-1 A, acosh(theta / delta), and the factor of
+  // the a-priori step count (sqrt(max / min of diag A) over a safety margin)
+  float cheb_theta, cheb_delta, cheb_acosh, cheb_scale;
   float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
   // read-only mesh / operator data
   const float2* V;
@@ -53,6 +62,7 @@ struct IterArgs {
   const float* lumped;   // FEM nodal quadrature weight A(V_a)/3
   const float* cTe;      // B-spline coefficients of Te, dense W x H
   const __nv_bfloat16* cTe16;   // BF16 copy of cTe read instead when non-null
+  const __half* cTeh;           // FP16 copy of cTe read instead when non-null
   const float* ReV;      // Re at the undeformed nodes
   const float* ReQ;      // Re at the undeformed edge midpoints
   // mutable state
@@ -64,7 +74,9 @@ struct IterArgs {
   float2* u_keep;        // S0 (grid engine): when set, u at the start of each iteration
                          // of the launch, (n_iters x nV), for the unrolled adjoint
   float2* hq;            // edge form: per-edge force contribution
-  float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s}
+  float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s};
+                         // the Chebyshev solve keeps its own state in the same
+                         // memory (b: 2 x nV float4, x: 2 x nV float2, d: nV float2)
   float2* rt;            // true residual (FP32 copy) for restarts
   float4* b;             // right-hand side, float-float {x.hi, x.lo, y.hi, y.lo}
   // reductions / control
@@ -72,6 +84,12 @@ struct IterArgs {
   unsigned long long* bar;  // barrier counter (zeroed before each launch)
   int* status;           // device status bits
   uint64_t barrier_timeout_ns;   // bound of every grid-barrier wait
+  // grid engine, S1 by Chebyshev: neighbour synchronisation of the steps
+  // (nullptr: the grid barrier).  nflags: one per block, zeroed before each
+  // launch; nbr_idx: kMaxNbr entries per block; nbr_cnt: entries used
+  unsigned* nflags;
+  const int* nbr_idx;
+  const int* nbr_cnt;
   int stall_block;       // failure-path test: this block skips its arrival at
   int stall_barrier;     // grid barrier number stall_barrier (0 = never)
   double* energy_hist;   // per-iteration data energy (hist_cap entries)
@@ -91,6 +109,7 @@ struct WarpArgs {
   const float2* u;
   const float* cTe;
   const __nv_bfloat16* cTe16;   // BF16 copy of cTe read instead when non-null
+  const __half* cTeh;           // FP16 copy of cTe read instead when non-null
   const float* Re;       // dense W x H reference pixels
   float* out;            // optional registered image
   float* part;           // one reduction record (kRec floats) per block
@@ -129,6 +148,7 @@ cudaError_t launch_sample_edges(const float* coef, int W, int H, const float2* V
 cudaError_t launch_pixel_map(const float2* V, const int* tri, int nT, int W, int H, int* pix_tri,
                              int* uncovered, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s);
+cudaError_t launch_to_fp16(const float* src, int64_t n, __half* dst, cudaStream_t s);
 cudaError_t launch_count_nonfinite(const float* img, int W, int H, int64_t stride, int* count,
                                    cudaStream_t s);
 cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, double* msd_out,
@@ -143,6 +163,7 @@ struct UnrollArgs {
   const int* adj_col;
   const float* cTe;
   const __nv_bfloat16* cTe16;
+  const __half* cTeh;
   const float* ReV;
 };
 // The adjoint recursion of an unrolled run of n_iters explicit iterations:
@@ -161,6 +182,17 @@ cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tp
                              const int* inc_ptr, const int* inc_tri, int nV, double* energy_out,
                              float2* grad_out, cudaStream_t s);
 
+// y = A x with the semi-implicit system matrix of form (S1, or S2 with the
+// stored entries); x, y: nV float2.  Batched: packed x, y over the pairs,
+// blocks of operator_tile_nodes() nodes of one pair each (tiles: (pair,
+// first node)).
+cudaError_t launch_apply_operator(int form, const IterArgs& a, const float2* x, float2* y,
+                                  int num_sms, cudaStream_t s);
+cudaError_t launch_batch_apply_operator(int form, const IterArgs* args, const int* node_off,
+                                        const int2* tiles, int n_tiles, const float2* x,
+                                        float2* y, cudaStream_t s);
+int operator_tile_nodes();
+
 // Iteration kernel: occupancy query and cooperative launch.
 // The data term and the regulariser of Eq. 1 at a.u into out[0], out[1]
 // (part: 2 doubles per block of scratch).
@@ -168,11 +200,18 @@ cudaError_t launch_energy_terms(int form, const IterArgs& a, int grid, double* p
                                 cudaStream_t s);
 
 // minb: register budget sized for 1 or 2 blocks per SM; lanes: lanes of a
-// warp per node (2: implicit forms with minb 1 only)
-cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes,
+// warp per node (2: implicit forms with minb 1 only); cheb: the S1 solve by
+// Chebyshev semi-iteration
+cudaError_t iterate_max_blocks(int form, int grad, int block, int minb, int lanes, bool cheb,
                                int* max_blocks_per_sm);
-cudaError_t launch_iterate(int form, int grad, int minb, int lanes, const IterArgs& a, int grid,
-                           int block, cudaStream_t s);
+cudaError_t launch_iterate(int form, int grad, int minb, int lanes, bool cheb, const IterArgs& a,
+                           int grid, int block, cudaStream_t s);
+// The neighbour blocks of every block of an iteration launch of grid x block
+// threads with lanes lanes per node (nbr_idx: grid x kMaxNbr, nbr_cnt: grid;
+// a count above kMaxNbr means the list did not fit).
+cudaError_t launch_neighbour_blocks(const int* adj_ptr, const int* adj_col, int nV, int grid,
+                                    int block, int lanes, int* nbr_idx, int* nbr_cnt,
+                                    cudaStream_t s);
 
 // ---------------------------------------------------------------- batched
 // Many registrations in one launch sequence.  Every per-kind array (pixels,
@@ -228,16 +267,16 @@ struct BatchWarpArgs {
 
 constexpr int kBatchTilePx = 4096;   // pixels per warp tile
 
-cudaError_t batch_prepare(int form, int grad, int block, int minb);
+cudaError_t batch_prepare(int form, int grad, int block, int minb, bool cheb);
 cudaError_t batch_setup(const BatchSetupArgs& a, bool edges, cudaStream_t s);
 cudaError_t batch_pixel_map(const BatchSetupArgs& a, int* pix_all, int64_t n_px, cudaStream_t s);
 cudaError_t batch_count_uncovered(const BatchSetupArgs& a, const int64_t* px_off, int64_t n_px,
                                   const int* pix_tri, int* counts, cudaStream_t s);
 // minb: the iteration kernel's register budget, sized for 1 or 2 CTAs per SM
-cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb,
+cudaError_t batch_max_teams(int form, int grad, int team_ctas, int block, int minb, bool cheb,
                             int* max_teams);
 cudaError_t batch_launch_iterate(int form, int grad, const BatchArgs& b, int n_teams, int block,
-                                 int minb, cudaStream_t s);
+                                 int minb, bool cheb, cudaStream_t s);
 cudaError_t batch_warp_msd(const BatchWarpArgs& a, cudaStream_t s);
 
 }  // namespace mreg

@@ -83,11 +83,36 @@ __global__ void k_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat1
 
 }  // namespace
 
+// FP16 copy of the coefficients (round to nearest even), 8 values per thread.
+__global__ void k_to_fp16(const float* __restrict__ src, int64_t n, __half* __restrict__ dst) {
+  const int64_t n8 = n / 8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n8;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n8) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(src) + 2 * i);
+      const float4 b = __ldg(reinterpret_cast<const float4*>(src) + 2 * i + 1);
+      __half2 o[4] = {__floats2half2_rn(a.x, a.y), __floats2half2_rn(a.z, a.w),
+                      __floats2half2_rn(b.x, b.y), __floats2half2_rn(b.z, b.w)};
+      reinterpret_cast<uint4*>(dst)[i] = *reinterpret_cast<const uint4*>(o);
+    } else {
+      for (int64_t k = 8 * n8; k < n; ++k) dst[k] = __float2half_rn(src[k]);
+    }
+  }
+}
+
 cudaError_t launch_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t n8 = n / 8 + 1;
   const int grid = (int)std::min<int64_t>((n8 + 255) / 256, 4096);
   k_to_bf16<<<grid, 256, 0, s>>>(src, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_fp16(const float* src, int64_t n, __half* dst, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t n8 = n / 8 + 1;
+  const int grid = (int)std::min<int64_t>((n8 + 255) / 256, 4096);
+  k_to_fp16<<<grid, 256, 0, s>>>(src, n, dst);
   return cudaGetLastError();
 }
 

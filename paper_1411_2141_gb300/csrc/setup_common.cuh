@@ -268,8 +268,9 @@ __device__ __forceinline__ bool warp_pixel(const WarpArgs& a, int64_t p, float& 
   pixel_barycentric(Va, Vb, Vc, x, y, la, lb, lc);
   const float ux = la * ua.x + lb * ub.x + lc * uc.x;
   const float uy = la * ua.y + lb * ub.y + lc * uc.y;
-  R = a.cTe16 ? spline_sample<GRAD>(a.cTe16, W, H, x, y, ux, uy, gx, gy)
-              : spline_sample<GRAD>(a.cTe, W, H, x, y, ux, uy, gx, gy);
+  R = with_te_coef(a, [&](const auto* c) {
+    return spline_sample<GRAD>(c, W, H, x, y, ux, uy, gx, gy);
+  });
   d = R - __ldg(a.Re + p);
   return true;
 }

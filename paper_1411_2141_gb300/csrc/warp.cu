@@ -372,10 +372,9 @@ __device__ __forceinline__ float2 adjoint_step_node(const UnrollArgs& a, const f
   split_coord(V.x, bx, ox);
   split_coord(V.y, by, oy);
   HessTaps taps;
-  if (a.cTe16)
-    hessian_taps(a.cTe16, a.W, a.H, bx, by, ox + u.x, oy + u.y, taps);
-  else
-    hessian_taps(a.cTe, a.W, a.H, bx, by, ox + u.x, oy + u.y, taps);
+  with_te_coef(a, [&](const auto* c) {
+    hessian_taps(c, a.W, a.H, bx, by, ox + u.x, oy + u.y, taps);
+  });
   const float rv = __ldg(a.ReV + j);
   const float2 w = smooth_t_node(a, vin, j);
   float f, gx, gy, hxx, hxy, hyy;
@@ -396,7 +395,7 @@ __global__ void __launch_bounds__(kUnrollBlock) k_unroll_adjoint(
     const UnrollArgs a, const float2* __restrict__ ustates, int n_iters, int passes, float2* va,
     float2* vb, float2* vc, unsigned long long* bar, int* status) {
   __shared__ int s_flag;
-  GridBarrier gb{bar, status, (unsigned long long)gridDim.x, 0ull, kBarrierTimeoutNs, 0ull};
+  GridBarrier gb{bar, status, (unsigned long long)gridDim.x, 0ull, kBarrierTimeoutNs};
   if (ld_volatile_i32(status) & kStatusAbort) return;   // an earlier launch gave up
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (int k = n_iters - 1; k >= 0; --k) {
@@ -482,7 +481,10 @@ cudaError_t launch_warp_msd(const WarpArgs& a, int grid, double inv_count, doubl
     const int gt = (a.nT + 255) / 256 < 8192 ? (a.nT + 255) / 256 : 8192;
     k_tri_affine<<<gt, 256, 0, s>>>(a);
   }
-  if (a.cTe16) {
+  if (a.cTeh) {
+    if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a, a.cTeh);
+    else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a, a.cTeh);
+  } else if (a.cTe16) {
     if (a.out) k_warp_msd<true><<<grid, kWarpBlock, 0, s>>>(a, a.cTe16);
     else k_warp_msd<false><<<grid, kWarpBlock, 0, s>>>(a, a.cTe16);
   } else {

@@ -51,7 +51,7 @@ MREG_FIELD_PIXEL_TRI = 6
 MREG_FIELD_ENERGY = 7
 MREG_FIELD_PCG_ITERS = 8
 MREG_FIELD_PCG_RESID = 9
-MREG_FIELD_COEF_TE_BF16 = 10
+MREG_FIELD_COEF_TE_16 = 10
 
 MODES = {"S0": MREG_MODE_EXPLICIT, "S1": MREG_MODE_UMBRELLA_IMPLICIT, "S2": MREG_MODE_FEM_IMPLICIT}
 GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
@@ -59,6 +59,14 @@ QUADS = {"Q0": MREG_QUAD_NODES, "Q1": MREG_QUAD_EDGE_MIDPOINTS}
 MREG_ENGINE_AUTO = 0
 MREG_ENGINE_GRID = 1
 ENGINES = {"auto": MREG_ENGINE_AUTO, "grid": MREG_ENGINE_GRID}
+MREG_COEFF_FP32 = 0
+MREG_COEFF_BF16 = 1
+MREG_COEFF_FP16 = 2
+COEFFS = {"fp32": MREG_COEFF_FP32, "bf16": MREG_COEFF_BF16, "fp16": MREG_COEFF_FP16}
+MREG_SOLVER_AUTO = 0
+MREG_SOLVER_CG = 1
+MREG_SOLVER_CHEBYSHEV = 2
+SOLVERS = {"auto": MREG_SOLVER_AUTO, "cg": MREG_SOLVER_CG, "chebyshev": MREG_SOLVER_CHEBYSHEV}
 
 
 class mreg_mesh(C.Structure):
@@ -79,9 +87,10 @@ class mreg_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("grad", C.c_int32), ("quad", C.c_int32),
                 ("pcg_maxit", C.c_int32), ("lambda_", C.c_double), ("pcg_rtol", C.c_double),
                 ("block_size", C.c_int32), ("grid_blocks", C.c_int32), ("engine", C.c_int32),
-                ("coeff_bf16", C.c_int32), ("team_ctas", C.c_int32),
+                ("coeff_storage", C.c_int32), ("team_ctas", C.c_int32),
                 ("smooth_passes", C.c_int32), ("host_topology", C.c_int32),
                 ("team_blocks_per_sm", C.c_int32), ("node_lanes", C.c_int32),
+                ("solver", C.c_int32), ("neighbour_sync", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
@@ -92,14 +101,14 @@ class mreg_stats_t(C.Structure):
                 ("last_rel_resid", C.c_double), ("last_energy", C.c_double),
                 ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
                 ("device_status", C.c_int32), ("engine", C.c_int32),
-                ("node_lanes", C.c_int32)]
+                ("node_lanes", C.c_int32), ("neighbour_sync", C.c_int32)]
 
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
            "mreg_msd", "mreg_energy", "mreg_energy_terms", "mreg_get_u", "mreg_set_u", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
            "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
-           "mreg_test_barrier_timeout",
+           "mreg_test_barrier_timeout", "mreg_apply_operator", "mreg_batch_apply_operator",
            "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
            "mreg_batch_shape", "mreg_batch_iterate_ms", "mreg_batch_msd", "mreg_batch_get_field",
            "mreg_batch_stats", "mreg_batch_destroy"]
@@ -147,6 +156,8 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_warp_energy_grad": ([vp, vp, vp, vp, vp], i32),
         "mreg_unroll_grad": ([vp, vp, i32, vp, vp, vp], i32),
         "mreg_test_barrier_timeout": ([vp, i32, i32, i64], i32),
+        "mreg_apply_operator": ([vp, vp, vp, vp], i32),
+        "mreg_batch_apply_operator": ([vp, vp, vp, vp], i32),
         "mreg_batch_create": ([i32, C.POINTER(mreg_mesh), C.POINTER(mreg_image),
                                C.POINTER(mreg_image), dbl, dbl, C.POINTER(mreg_options), vp,
                                C.POINTER(vp)], i32),
@@ -220,9 +231,9 @@ def default_options() -> mreg_options:
 
 def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_maxit=None,
                  block_size=0, grid_blocks=0, engine="auto",
-                 coeff_bf16=False, team_ctas=0, team_blocks_per_sm=0,
-                 smooth_passes=0, host_topology=False, node_lanes=0,
-                 allocator=None) -> mreg_options:
+                 coeff_bf16=False, coeff="fp32", team_ctas=0, team_blocks_per_sm=0,
+                 smooth_passes=0, host_topology=False, node_lanes=0, solver="auto",
+                 neighbour_sync=False, allocator=None) -> mreg_options:
     o = default_options()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.grad = GRADS[grad] if isinstance(grad, str) else int(grad)
@@ -236,10 +247,16 @@ def make_options(mode="S0", grad="G0", quad="Q0", lam=None, pcg_rtol=None, pcg_m
     o.block_size = int(block_size)
     o.grid_blocks = int(grid_blocks)
     o.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
-    o.coeff_bf16 = int(bool(coeff_bf16))
+    # coeff: storage of Te's coefficients ("fp32", "bf16", "fp16");
+    # coeff_bf16=True is the same as coeff="bf16"
+    o.coeff_storage = MREG_COEFF_BF16 if coeff_bf16 else (COEFFS[coeff] if isinstance(coeff, str)
+                                                          else int(coeff))
     o.team_ctas = int(team_ctas)
     o.team_blocks_per_sm = int(team_blocks_per_sm)
     o.node_lanes = int(node_lanes)
+    o.solver = SOLVERS[solver] if isinstance(solver, str) else int(solver)
+    o.neighbour_sync = int(bool(neighbour_sync)) if isinstance(neighbour_sync, bool) \
+        else int(neighbour_sync)
     o.smooth_passes = int(smooth_passes)
     o.host_topology = int(bool(host_topology))
     if allocator is not None:
@@ -348,6 +365,17 @@ class Registration:
     def step(self, n_iters: int, stream=None):
         _check(load().mreg_step(self._h, int(n_iters), _stream_ptr(stream)), "mreg_step")
 
+    def apply_operator(self, x, y, stream=None):
+        """y = A x with the semi-implicit system matrix (asynchronous); x, y:
+        contiguous (n_nodes, 2) float32 device tensors."""
+        for t in (x, y):
+            if not _is_torch_cuda(t) or str(t.dtype) != "torch.float32" or not t.is_contiguous() \
+                    or tuple(t.shape) != (self.n_nodes, 2):
+                raise ValueError("x and y must be contiguous (n_nodes, 2) float32 device tensors")
+        _check(load().mreg_apply_operator(self._h, x.data_ptr(), y.data_ptr(), _stream_ptr(stream)),
+               "mreg_apply_operator")
+        return y
+
     def test_barrier_timeout(self, block: int, barrier: int, timeout_ns: int):
         """Arm the next iteration launch to run out of one grid-barrier wait
         (a test of the failure path; see mreg_test_barrier_timeout)."""
@@ -428,7 +456,7 @@ class Registration:
                "mreg_get_field")
         dtype = {MREG_FIELD_PIXEL_TRI: np.int32, MREG_FIELD_PCG_ITERS: np.int32,
                  MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64,
-                 MREG_FIELD_COEF_TE_BF16: np.uint16}.get(field, np.float32)
+                 MREG_FIELD_COEF_TE_16: np.uint16}.get(field, np.float32)
         out = np.empty(n.value, dtype)
         if n.value:
             _check(lib.mreg_get_field(self._h, field, out.ctypes.data, 0, None, _stream_ptr(stream)),
@@ -436,7 +464,7 @@ class Registration:
         if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
             out = out.reshape(-1, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
-                field == MREG_FIELD_COEF_TE_BF16 and n.value):
+                field == MREG_FIELD_COEF_TE_16 and n.value):
             out = out.reshape(self.height, self.width)
         return out
 
@@ -452,7 +480,7 @@ class Registration:
 
 _FIELD_DTYPES = {MREG_FIELD_PIXEL_TRI: np.int32, MREG_FIELD_PCG_ITERS: np.int32,
                  MREG_FIELD_ENERGY: np.float64, MREG_FIELD_PCG_RESID: np.float64,
-                 MREG_FIELD_COEF_TE_BF16: np.uint16}
+                 MREG_FIELD_COEF_TE_16: np.uint16}
 
 
 class Batch:
@@ -517,6 +545,18 @@ class Batch:
     def run(self, n_iters: int, stream=None):
         _check(load().mreg_batch_run(self._h, int(n_iters), _stream_ptr(stream)), "mreg_batch_run")
 
+    def apply_operator(self, x, y, stream=None):
+        """y = A x for every pair (asynchronous); x, y: contiguous
+        (sum of n_nodes, 2) float32 device tensors packed in pair order."""
+        n = sum(self.n_nodes)
+        for t in (x, y):
+            if not _is_torch_cuda(t) or str(t.dtype) != "torch.float32" or not t.is_contiguous() \
+                    or tuple(t.shape) != (n, 2):
+                raise ValueError("x and y must be contiguous (total nodes, 2) float32 device tensors")
+        _check(load().mreg_batch_apply_operator(self._h, x.data_ptr(), y.data_ptr(),
+                                                _stream_ptr(stream)), "mreg_batch_apply_operator")
+        return y
+
     def tune(self, n_iters: int, stream=None):
         """Autotune the team shape; returns ((team_ctas, block_size,
         blocks_per_sm), times) with times[(ctas, block, per_sm)] in ms (None
@@ -564,7 +604,7 @@ class Batch:
         if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
             out = out.reshape(-1, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
-                field == MREG_FIELD_COEF_TE_BF16 and n.value):
+                field == MREG_FIELD_COEF_TE_16 and n.value):
             out = out.reshape(self.shapes[pair])
         return out
 

@@ -146,6 +146,11 @@ def test_option_validation_of_the_newer_fields(lib):
     _expect(E.MREG_ERR_INVALID_ARG,
             lambda: _create(V, T, img, img, mode="S1", node_lanes=2, team_blocks_per_sm=2))
     _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, engine=2))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S1", solver=3))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S2", grad="G1",
+                                                    solver="chebyshev"))
+    _expect(E.MREG_ERR_INVALID_ARG, lambda: _create(V, T, img, img, mode="S0",
+                                                    solver="chebyshev"))
     _expect(E.MREG_ERR_INVALID_ARG, lambda: mreg.Batch([(V, T, img, img)], 0.1, 1.0, mode="S1",
                                                        node_lanes=2))
     o = mreg.make_options(host_topology=True)
@@ -158,7 +163,9 @@ def test_option_validation_of_the_newer_fields(lib):
     assert lib.mreg_create(C.byref(mesh), C.byref(im), C.byref(im), 0.1, 1.0, C.byref(o), None,
                            C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
     o = mreg.make_options(coeff_bf16=True)
-    o.coeff_bf16 = 3
+    assert o.coeff_storage == mreg.MREG_COEFF_BF16
+    assert mreg.make_options(coeff="fp16").coeff_storage == mreg.MREG_COEFF_FP16
+    o.coeff_storage = 3
     assert lib.mreg_create(C.byref(mesh), C.byref(im), C.byref(im), 0.1, 1.0, C.byref(o), None,
                            C.byref(h)) == mreg.MREG_ERR_INVALID_ARG
     assert lib.mreg_warp_energy_grad(None, None, None, None, None) == mreg.MREG_ERR_INVALID_ARG

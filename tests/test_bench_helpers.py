@@ -68,6 +68,21 @@ def test_algorithmic_bytes_model():
     # proportional to the mesh size
     s1_big = bench.algorithmic_bytes_per_iteration(2 * n_v, 2 * n_t, 2 * nnz, "S1", 4.0)
     assert abs(s1_big - 2 * s1_4) < 1e-6 * s1_big
+    # Chebyshev: the first step is in the force phase; each further step moves
+    # the graph, x, b, d and the Jacobi entries (~80 B/node), far less than a
+    # CG step (the CG state of every neighbour)
+    c1 = bench.algorithmic_bytes_per_iteration(n_v, n_t, nnz, "S1", 1.0, "chebyshev")
+    c5 = bench.algorithmic_bytes_per_iteration(n_v, n_t, nnz, "S1", 5.0, "chebyshev")
+    assert 60 <= (c5 - c1) / 4 / n_v <= 100
+    assert c1 > s1_0 - 1e-6 and c5 < s1_4
+
+
+def test_solver_names():
+    ns = types.SimpleNamespace
+    assert bench.solver_of(ns(mode="S1", solver="auto")) == "chebyshev"
+    assert bench.solver_of(ns(mode="S1", solver="cg")) == "cg"
+    assert bench.solver_of(ns(mode="S2", solver="auto")) == "cg"
+    assert bench.solver_of(ns(mode="S0", solver="auto")) == "none"
 
 
 def test_launch_counts_match_the_measured_launch_lists():

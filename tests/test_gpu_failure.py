@@ -38,17 +38,24 @@ def c0():
     return inputs.make_case(inputs.config_spec(0))
 
 
-def _reg(mreg, case, mode, grad="G0"):
+def _reg(mreg, case, mode, grad="G0", **kw):
     return mreg.Registration(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
-                             mode=mode, grad=grad)
+                             mode=mode, grad=grad, **kw)
 
 
-@pytest.mark.parametrize("mode,barrier", [("S0", 3), ("S1", 1), ("S1", 7)])
-def test_barrier_timeout_is_reported_and_reset_recovers(mreg, c0, mode, barrier):
+# Synchronisation numbers of an S1 launch (Chebyshev solve): 1 after the
+# iterate is copied in, 2 after the first sample, 3 after the force phase of
+# iteration 0 (grid barriers), then the solve's steps (the neighbour
+# synchronisation when nsync, else grid barriers): 5 and 7 fall on steps, in
+# the first and the second solve.
+@pytest.mark.parametrize("mode,barrier,nsync", [("S0", 3, True), ("S1", 1, True),
+                                                ("S1", 5, True), ("S1", 7, True),
+                                                ("S1", 5, False)])
+def test_barrier_timeout_is_reported_and_reset_recovers(mreg, c0, mode, barrier, nsync):
     with _reg(mreg, c0, mode) as ref:
         ref.step(10)
         u_ref = ref.get_u()
-    with _reg(mreg, c0, mode) as r:
+    with _reg(mreg, c0, mode, neighbour_sync=nsync) as r:
         grid = r.stats()["grid_blocks"]
         r.test_barrier_timeout(grid - 1, barrier, TIMEOUT_NS)
         r.step(10)

@@ -283,12 +283,16 @@ def test_zero_iterations_and_tiny_image(mreg):
             assert abs(r.msd() - pb.msd(u_ref)) <= 1e-5 * max(pb.msd(u_ref), 1e-12)
 
 
-def test_pcg_cap_is_reported(mreg, c0):
-    with _reg(mreg, c0, "S1", pcg_maxit=1, pcg_rtol=1e-12) as r:
+@pytest.mark.parametrize("mode,solver", [("S1", "chebyshev"), ("S1", "cg"), ("S2", "auto")])
+def test_pcg_cap_is_reported(mreg, c0, mode, solver):
+    with _reg(mreg, c0, mode, "G1" if mode == "S2" else "G0", pcg_maxit=1, pcg_rtol=1e-12,
+              solver=solver) as r:
         r.step(3)
         st = r.stats(check=False)
+        its = r.get_field(mreg.MREG_FIELD_PCG_ITERS)
     assert st["status"] == mreg.MREG_ERR_NOT_CONVERGED
     assert st["not_converged"] == 3 and st["max_pcg_iters"] == 1
+    assert (its == 1).all()
 
 
 # ---------------------------------------------------------------- extras
@@ -516,9 +520,10 @@ def test_warp_on_ragged_images(mreg, hw, amp):
 
 
 # ------------------------------------------------ the solve's stated residual
-@pytest.mark.parametrize("mode,grad,quad", [("S1", "G0", "Q0"), ("S1", "G1", "Q0"),
-                                            ("S2", "G0", "Q0"), ("S2", "G1", "Q1")])
-def test_solve_residual_recomputed_in_fp64(mreg, c0, c1, mode, grad, quad):
+@pytest.mark.parametrize("mode,grad,quad,solver", [
+    ("S1", "G0", "Q0", "auto"), ("S1", "G1", "Q0", "auto"), ("S1", "G0", "Q0", "cg"),
+    ("S2", "G0", "Q0", "auto"), ("S2", "G1", "Q1", "auto")])
+def test_solve_residual_recomputed_in_fp64(mreg, c0, c1, mode, grad, quad, solver):
     """The stopping rule of the semi-implicit solve, ||b - A u'||_2 <=
     rtol ||b||_2 per component, recomputed on the host in FP64 from what the
     library hands out: u before and after one step and the force that step
@@ -527,12 +532,13 @@ def test_solve_residual_recomputed_in_fp64(mreg, c0, c1, mode, grad, quad):
     pairs).  S2: b = M u - tau F_w, A = M + l K, with the FP32 matrix entries
     the kernel is given (the FP64 assembly rounded to FP32, as here).  The
     step is taken from a state 20 iterations in, on both the 128^2 and the
-    512^2 pair."""
+    512^2 pair.  S1 runs both solvers (Chebyshev semi-iteration by default,
+    CG on request)."""
     import scipy.sparse as sp
     rtol = 1e-7
     for case in (c0, c1):
         pb = _oracle(case, mode, grad, quad)
-        with _reg(mreg, case, mode, grad, quad) as r:
+        with _reg(mreg, case, mode, grad, quad, solver=solver) as r:
             r.step(20)
             u = r.get_u().astype(np.float64)
             r.step(1)
@@ -550,7 +556,55 @@ def test_solve_residual_recomputed_in_fp64(mreg, c0, c1, mode, grad, quad):
             b = M32 @ u - tau * F
         res = b - A @ u1
         rel = np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)
-        print(f"{mode}{grad}{quad} {case.spec.side}^2: FP64 residual {rel.max():.2e}, "
+        print(f"{mode}{grad}{quad} {solver} {case.spec.side}^2: FP64 residual {rel.max():.2e}, "
               f"reported {reported[-1]:.2e}")
         assert (rel <= rtol).all()
         assert reported[-1] <= rtol
+
+
+@pytest.mark.parametrize("grad", ["G0", "G1"])
+def test_umbrella_solvers_agree(mreg, c0, c1, grad):
+    """S1 solved by Chebyshev semi-iteration (the default) and by CG: every
+    solve of both meets the verified residual bound, both registrations meet
+    the parity bar against the oracle's direct solve (and so agree with each
+    other to within it).  The Chebyshev step counts stay small (the
+    spectrum of the Jacobi-scaled matrix lies in [1/(1+l), (1+2l)/(1+l)])."""
+    for case in (c0, c1):
+        n = case.spec.n_iter
+        pb = _oracle(case, "S1", grad)
+        u_ref, _ = pb.run(n)
+        out = {}
+        for solver in ("cg", "chebyshev"):
+            with _reg(mreg, case, "S1", grad, solver=solver) as r:
+                r.step(n)
+                st = r.stats()
+                out[solver] = (r.get_u(), r.get_field(mreg.MREG_FIELD_PCG_ITERS),
+                               r.get_field(mreg.MREG_FIELD_PCG_RESID), st)
+        for solver, (u, its, res, st) in out.items():
+            du = np.abs(u - u_ref).max()
+            print(f"S1{grad} {solver} {case.spec.side}^2: du={du:.2e} steps mean "
+                  f"{its.mean():.2f} max {its.max()} resid max {res.max():.2e}")
+            assert du <= U_TOL
+            assert len(res) == n and (res <= 1e-7).all()
+            assert st["not_converged"] == 0
+        assert np.abs(out["cg"][0] - out["chebyshev"][0]).max() <= U_TOL
+        assert out["chebyshev"][1].mean() <= 8
+
+
+@pytest.mark.parametrize("grad", ["G0", "G1"])
+def test_neighbour_sync_changes_no_bit(mreg, c0, c1, grad):
+    """The Chebyshev steps synchronise each block only with the blocks that
+    own its nodes' neighbours; that changes when a block may proceed, never
+    what it computes, so the registration is bitwise the same as with the
+    grid barrier after every step (and so, through the parity tests, the
+    oracle's)."""
+    for case in (c0, c1):
+        out = []
+        for ns in (True, False):
+            with _reg(mreg, case, "S1", grad, neighbour_sync=ns) as r:
+                assert r.stats()["neighbour_sync"] == (1 if ns else 0)
+                r.step(case.spec.n_iter)
+                out.append((r.get_u(), r.msd(), r.get_field(mreg.MREG_FIELD_PCG_ITERS)))
+        assert np.array_equal(out[0][0], out[1][0])
+        assert out[0][1] == out[1][1]
+        assert np.array_equal(out[0][2], out[1][2])
