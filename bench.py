@@ -82,6 +82,9 @@ def parse():
                    help="differentiation form and --single: CUDA streams the pairs are spread over")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--operator", action="store_true",
+                   help="config 3: also time the batched system-matrix product y = A x (the "
+                        "standalone SpMV) against the HBM roofline")
     p.add_argument("--no-forms", action="store_true",
                    help="config 1: skip the short runs of the batched, plain-on-streams and "
                         "differentiation forms")
@@ -354,6 +357,7 @@ PROFILE_C2 = ("k_implicit_2048px_250k_nodes.md",
               ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "iterate.cu",
                "mreg_internal.h"])
 PROFILE_ONE_PAIR = {1: PROFILE_C1, 2: PROFILE_C2}
+PROFILE_OP = ("k_batch_apply_256_uneven_pairs.md", ["operator.cu", "mreg_internal.h"])
 PROFILE_C3 = ("k_batch_256_uneven_pairs.md",
               ["device_common.cuh", "iterate_common.cuh", "iterate_body.cuh", "batch.cu",
                "setup_common.cuh", "mreg_internal.h"])
@@ -672,6 +676,47 @@ def run_ours_batch_single(args, rank, world, local_rank, cases=None):
     return line
 
 
+def operator_bytes(n_v: int, nnz: int, mode: str) -> float:
+    """Compulsory bytes of y = A x for one mesh: the row pointers and column
+    indices (and for S2 the stored off-diagonal values and diagonal), x read
+    once and y written once (both float2)."""
+    vals = (4 * nnz + 4 * n_v) if mode == "S2" else 0
+    return 4 * (n_v + 1) + 4 * nnz + vals + 8 * n_v + 8 * n_v
+
+
+def measure_operator(b, cases, nnz, mode, dev, stream, flush, launches: int = 20) -> dict:
+    """The batched operator y = A x (every pair's system matrix, one launch)
+    timed with CUDA events on the launching stream, L2 flushed before each
+    launch, against the HBM roofline."""
+    import torch
+    n = sum(c.n_nodes for c in cases)
+    g = torch.Generator(device=dev).manual_seed(11)
+    x = torch.randn((n, 2), dtype=torch.float32, device=dev, generator=g)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        b.apply_operator(x, y, stream)
+    evs = []
+    for k in range(launches):
+        flush.fill_(k & 0xFF)
+        a_ev = torch.cuda.Event(enable_timing=True)
+        e_ev = torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        b.apply_operator(x, y, stream)
+        e_ev.record(stream)
+        evs.append((a_ev, e_ev))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(e) for a, e in evs)
+    nbytes = sum(operator_bytes(c.n_nodes, z, mode) for c, z in zip(cases, nnz))
+    peak, peak_src = peak_hbm()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"kernel": "k_batch_apply (y = A x with every pair's system matrix, one launch)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": nbytes, "launch_ms": ms, "launches": launches,
+            "l2": "flushed before every launch (256 MiB write)",
+            "traffic": profiled_traffic(PROFILE_OP) if mode == "S1" and len(cases) == 256 else None}
+
+
 def run_ours_batch(args, rank, world, local_rank, cases=None):
     import torch
     from paper_1411_2141_gb300 import mreg
@@ -727,7 +772,7 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     msd = b.msd(stream)
     cg = []
-    nnz_total, per_iter_total = 0, 0.0
+    nnz_total, per_iter_total, nnzs = 0, 0.0, []
     for k, c in enumerate(cases):
         its = b.get_field(k, mreg.MREG_FIELD_PCG_ITERS)
         cgm = float(its.mean()) if args.mode != "S0" and len(its) else 0.0
@@ -735,9 +780,12 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
         e = np.sort(np.concatenate([c.T[:, [0, 1]], c.T[:, [1, 2]], c.T[:, [2, 0]]]), axis=1)
         nnz = 2 * len(np.unique(e, axis=0))
         nnz_total += nnz
+        nnzs.append(nnz)
         per_iter_total += algorithmic_bytes_per_iteration(c.n_nodes, c.n_tris, nnz, args.mode, cgm,
                                                           solver_of(args))
 
+    op = (measure_operator(b, cases, nnzs, args.mode, dev, stream, flush)
+          if getattr(args, "operator", False) and args.mode != "S0" else None)
     e2e = None
     if not args.no_e2e:
         pinned = [(c.V, c.T, torch.from_numpy(c.Re).pin_memory().numpy(),
@@ -802,6 +850,8 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
         "clocks": clk,
         "gpu_launches": BATCH_LAUNCHES * args.steps,
     }
+    if op is not None:
+        line["operator_roofline"] = op
     if e2e is not None:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
@@ -998,6 +1048,8 @@ def _form_summary(line: dict, what: str) -> dict:
         out["roofline"] = {k: line["roofline"][k] for k in ("kernel", "achieved", "frac", "peak")}
     if "team" in line.get("config", {}):
         out["team"] = line["config"]["team"]
+    if "operator_roofline" in line:
+        out["operator_roofline"] = line["operator_roofline"]
     return out
 
 
@@ -1011,7 +1063,9 @@ def run_forms(args, rank, world, local_rank) -> dict | None:
     cases = batch_cases()
     forms = {}
     sub.config = 3
+    sub.operator = True
     line = run_ours_batch(sub, rank, world, local_rank, cases)
+    sub.operator = False
     if line is not None:
         forms["batched_fp32"] = _form_summary(
             line, "config 3: 256 uneven pairs, 100 iterations each, batched engine (one CUDA-graph "

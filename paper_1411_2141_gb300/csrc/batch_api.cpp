@@ -247,7 +247,8 @@ mreg_status mreg_batch_apply_operator(mreg_batch* b, const float* x_dev, float* 
     b->n_op_tiles = (int)tiles.size();
   }
   CK(mreg::launch_batch_apply_operator(b->form, b->d_args, b->setup.node_off, b->op_tiles,
-                                       b->n_op_tiles, (const float2*)x_dev, (float2*)y_dev, s),
+                                       b->n_op_tiles, (const float2*)x_dev, (float2*)y_dev,
+                                       b->num_sms, s),
      "operator kernel launch");
   return MREG_OK;
 }

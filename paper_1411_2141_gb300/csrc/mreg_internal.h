@@ -190,7 +190,7 @@ cudaError_t launch_apply_operator(int form, const IterArgs& a, const float2* x, 
                                   int num_sms, cudaStream_t s);
 cudaError_t launch_batch_apply_operator(int form, const IterArgs* args, const int* node_off,
                                         const int2* tiles, int n_tiles, const float2* x,
-                                        float2* y, cudaStream_t s);
+                                        float2* y, int num_sms, cudaStream_t s);
 int operator_tile_nodes();
 
 // Iteration kernel: occupancy query and cooperative launch.

@@ -94,3 +94,9 @@ def test_launch_counts_match_the_measured_launch_lists():
     assert bench.launches_per_registration(args, 1100) == 14            # two 1024-iteration launches
     assert bench.launches_per_registration(types.SimpleNamespace(coeff="bf16"), 200) == 13
     assert bench.ADJOINT_LAUNCHES == 7
+
+
+def test_operator_bytes():
+    # S1: row pointers, columns, x and y; S2 adds the stored values and diagonal
+    assert bench.operator_bytes(10, 60, "S1") == 4 * 11 + 4 * 60 + 16 * 10
+    assert bench.operator_bytes(10, 60, "S2") == bench.operator_bytes(10, 60, "S1") + 4 * 60 + 40
