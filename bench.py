@@ -85,6 +85,9 @@ def parse():
     p.add_argument("--operator", action="store_true",
                    help="config 3: also time the batched system-matrix product y = A x (the "
                         "standalone SpMV) against the HBM roofline")
+    p.add_argument("--checkpoint", type=int, default=0,
+                   help="config 4: keep every C-th state of the unroll and recompute the "
+                        "segments in the backward pass (0: keep every state)")
     p.add_argument("--no-forms", action="store_true",
                    help="config 1: skip the short runs of the batched, plain-on-streams and "
                         "differentiation forms")
@@ -345,6 +348,27 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def pair_cost(case) -> float:
+    """Work of one pair when a batch is split over ranks: its node-iterations
+    plus its pixels (the set-up and the warp)."""
+    return float(case.n_nodes) * case.spec.n_iter + float(case.Re.size)
+
+
+def lpt_partition(costs, world: int) -> list[list[int]]:
+    """Greedy longest-processing-time split of independent pairs over ranks:
+    pairs in decreasing cost (ties by index), each to the rank with the
+    smallest total so far (ties: lowest rank).  Deterministic, so every rank
+    computes the same split; each rank's list is in ascending pair order."""
+    order = sorted(range(len(costs)), key=lambda k: (-costs[k], k))
+    load = [0.0] * world
+    parts: list[list[int]] = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(k)
+        load[r] += costs[k]
+    return [sorted(p) for p in parts]
+
+
 def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     """Units of all ranks per second of the slowest rank (weak scaling)."""
     return units_per_rank * world / seconds
@@ -560,6 +584,16 @@ BATCH_LAUNCHES = 9   # prefilter rows + columns, Re at nodes, pixel fill + map,
 ADJOINT_LAUNCHES = 7
 
 
+def adjoint_launches(n_iter: int, every: int) -> int:
+    """Kernels of one unrolled gradient with checkpoints every `every`
+    iterations (0: every state kept): per segment a forward launch and its
+    energy sums, and (when there are several segments) the recomputation
+    with its energy sums and one adjoint launch; the warp adjoint's three
+    passes and energy sum once."""
+    segs = 1 if every <= 0 or every >= n_iter else -(-n_iter // every)
+    return 4 + (2 * segs + segs if segs == 1 else 5 * segs)
+
+
 def batch_workload_config(args, cases, shape=None):
     sides = [c.spec.side for c in cases]
     nodes = [c.n_nodes for c in cases]
@@ -575,6 +609,9 @@ def batch_workload_config(args, cases, shape=None):
            "alpha": cases[0].spec.alpha, "tau": cases[0].spec.tau,
            "l2": "flushed between timed steps (256 MiB write); the packed batch (~1.3 GB) exceeds L2",
            "parallelism": f"replicas x{args.gpus} (the whole batch per GPU per step)"}
+    if args.gpus > 1:
+        cfg["parallelism"] = (f"the batch split over {args.gpus} GPUs by greedy LPT on "
+                              f"node-iterations + pixels; this config describes rank 0's share")
     if shape is not None:
         cfg["team"] = {"ctas": shape[0], "block": shape[1], "blocks_per_sm": shape[2],
                        "teams": shape[3]}
@@ -725,6 +762,10 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
     dev = torch.device("cuda", local_rank)
     mreg.load()
     cases = cases or batch_cases(args.pairs)
+    n_total = len(cases)
+    split = world > 1
+    if split:   # pairs are independent: each rank registers its LPT share of the batch
+        cases = [cases[k] for k in lpt_partition([pair_cost(c) for c in cases], world)[rank]]
     n_iter = cases[0].spec.n_iter
     stream = torch.cuda.current_stream()
     coeff = args.coeff
@@ -813,7 +854,8 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = sum(c.Re.nbytes + c.Te.nbytes + c.V.nbytes + c.T.nbytes for c in cases)
         d2h = 8 * len(cases) + sum(c.V.nbytes for c in cases)
-        e2e = {"value": whole_job_rate(e2e_steps * len(cases), world, e2e_s),
+        e2e = {"value": (e2e_steps * n_total / e2e_s if split
+                         else whole_job_rate(e2e_steps * len(cases), world, e2e_s)),
                "unit": "registrations/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
                "note": "each step creates the batch from pinned host arrays (host topology "
@@ -822,7 +864,9 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
     if rank != 0:
         b.close()
         return None
-    value = whole_job_rate(args.steps * len(cases), world, total_s)
+    # split: the ranks registered the n_total pairs together (strong scaling)
+    value = (args.steps * n_total / total_s if split
+             else whole_job_rate(args.steps * len(cases), world, total_s))
     it_ms = statistics.mean(iter_ms)
     achieved = per_iter_total * n_iter / (it_ms / 1e3) / 1e9
     peak, peak_src = peak_hbm()
@@ -830,7 +874,8 @@ def run_ours_batch(args, rank, world, local_rank, cases=None):
     line = {
         "metric": "registrations/s", "value": value, "unit": "registrations/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": batch_workload_config(args, cases, shape),
         "node_iters_per_s": value / len(cases) * sum(c.n_nodes for c in cases) * n_iter,
@@ -910,7 +955,8 @@ def run_ours_adjoint(args, rank, world, local_rank):
         for s in side:
             s.wait_stream(stream)
         for k, r in enumerate(regs):
-            r.unroll_grad(u0[k], K, E[k:k + 1], g[k], side[k % len(side)])
+            r.unroll_grad(u0[k], K, E[k:k + 1], g[k], side[k % len(side)],
+                          checkpoint_every=args.checkpoint)
         for s in side:
             stream.wait_stream(s)
     for _ in range(args.warmup):
@@ -968,7 +1014,7 @@ def run_ours_adjoint(args, rank, world, local_rank):
                 sk = side[k % len(side)]
                 with torch.cuda.stream(sk):
                     u0_d[k].copy_(u0_h[k], non_blocking=True)
-                    r.unroll_grad(u0_d[k], K, E[k:k + 1], g[k], sk)
+                    r.unroll_grad(u0_d[k], K, E[k:k + 1], g[k], sk, checkpoint_every=args.checkpoint)
                     g_h[k].copy_(g[k], non_blocking=True)
             for s in side:
                 stream.wait_stream(s)
@@ -1004,7 +1050,11 @@ def run_ours_adjoint(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"config4: {len(cases)} pairs of 256x256, {cases[0].n_nodes}-node "
                                f"meshes, gradient of the warp energy through {K} explicit "
-                               f"iterations (spline gradient) with respect to u0",
+                               f"iterations (spline gradient) with respect to u0"
+                               + (f", states checkpointed every {args.checkpoint} iterations "
+                                  f"(segments recomputed in the backward pass)"
+                                  if 0 < args.checkpoint < K else ", every state kept"),
+                   "checkpoint_every": args.checkpoint,
                    "pairs": len(cases), "iterations": K, "streams": len(side),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{args.gpus}"},
@@ -1016,7 +1066,7 @@ def run_ours_adjoint(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": statistics.mean(fw_bytes),
                      "launch_ms": statistics.mean(fw_ms), "traffic": None},
         "clocks": clk,
-        "gpu_launches": len(cases) * ADJOINT_LAUNCHES * args.steps,
+        "gpu_launches": len(cases) * adjoint_launches(K, args.checkpoint) * args.steps,
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -1086,11 +1136,15 @@ def run_forms(args, rank, world, local_rank) -> dict | None:
                   f"spread over {sub.streams} CUDA streams")
     del cases
     sub.config = 4
-    line = run_ours_adjoint(sub, rank, world, local_rank)
-    if line is not None:
-        forms["differentiation"] = _form_summary(
-            line, "config 4: gradient of the warp energy through 20 unrolled explicit iterations, "
-                  f"64 pairs of 256x256, {sub.streams} CUDA streams")
+    for every in (0, 5):
+        sub.checkpoint = every
+        line = run_ours_adjoint(sub, rank, world, local_rank)
+        if line is not None:
+            key = "differentiation" if every == 0 else "differentiation_checkpointed"
+            forms[key] = _form_summary(
+                line, "config 4: gradient of the warp energy through 20 unrolled explicit "
+                      f"iterations, 64 pairs of 256x256, {sub.streams} CUDA streams"
+                      + (f", states checkpointed every {every} iterations" if every else ""))
     return forms if rank == 0 else None
 
 

@@ -344,6 +344,21 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
 mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
                              double* energy_dev, float* grad_dev, void* stream);
 
+/* mreg_unroll_grad with checkpoints: only the starting state of every
+ * segment of checkpoint_every iterations is kept in the forward run; the
+ * backward pass recomputes each segment's states from its checkpoint (the
+ * same kernel and launch shape, so bitwise the forward run's states) and
+ * runs the adjoint recursion over them, last segment first.  The gradient
+ * and the energy are bitwise those of mreg_unroll_grad; the state memory is
+ * (ceil(K / c) + c + 1) instead of K vectors of 8 bytes per node, for one
+ * more forward run.  checkpoint_every = 0 or >= n_iters is mreg_unroll_grad.
+ * The handle's iterate is left at u_K; its per-iteration history fields
+ * describe the last segment run.  Errors: as mreg_unroll_grad, and
+ * INVALID_ARG for checkpoint_every < 0.                                      */
+mreg_status mreg_unroll_grad_checkpointed(mreg_handle* h, const float* u0_dev, int32_t n_iters,
+                                          int32_t checkpoint_every, double* energy_dev,
+                                          float* grad_dev, void* stream);
+
 /* MSD of the current displacement (abstract; Table 1): FP32 squared
  * differences summed in float-float, the mean taken and returned in FP64.
  * Blocks until the value is on the host.                                    */

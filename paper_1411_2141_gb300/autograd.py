@@ -51,11 +51,12 @@ class UnrolledWarpEnergy(torch.autograd.Function):
     library's adjoint recursion over the kept states."""
 
     @staticmethod
-    def forward(ctx, u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int) -> torch.Tensor:
+    def forward(ctx, u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int,
+                checkpoint_every: int = 0) -> torch.Tensor:
         uc = u0.detach().to(torch.float32).contiguous()
         energy = torch.empty(1, dtype=torch.float64, device=u0.device)
         grad = torch.empty_like(uc) if ctx.needs_input_grad[0] else None
-        reg.unroll_grad(uc, n_iters, energy, grad)
+        reg.unroll_grad(uc, n_iters, energy, grad, checkpoint_every=checkpoint_every)
         ctx.save_for_backward(grad)
         ctx.reg = reg
         return energy.reshape(())
@@ -64,13 +65,17 @@ class UnrolledWarpEnergy(torch.autograd.Function):
     def backward(ctx, g_energy: torch.Tensor):
         (grad,) = ctx.saved_tensors
         if grad is None:
-            return None, None, None
+            return None, None, None, None
         # the forward run is a persistent kernel with bounded grid-barrier
         # waits: raise (MregError, MREG_ERR_DEVICE_CHECK) if one gave up
         # rather than hand back a gradient of an unfinished run
         ctx.reg.stats()
-        return (grad * g_energy.to(grad.dtype)), None, None
+        return (grad * g_energy.to(grad.dtype)), None, None, None
 
 
-def unrolled_warp_energy(u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int) -> torch.Tensor:
-    return UnrolledWarpEnergy.apply(u0, reg, n_iters)
+def unrolled_warp_energy(u0: torch.Tensor, reg: "_mreg.Registration", n_iters: int,
+                         checkpoint_every: int = 0) -> torch.Tensor:
+    """E(u_K) with its gradient through the K iterations; checkpoint_every
+    > 0 keeps only every c-th state of the forward run and recomputes the
+    segments in the backward pass (the same gradient, bit for bit)."""
+    return UnrolledWarpEnergy.apply(u0, reg, n_iters, checkpoint_every)

@@ -893,21 +893,30 @@ mreg_status mreg_warp_energy_grad(mreg_handle* h, const float* u_dev, double* en
   return MREG_OK;
 }
 
-mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
-                             double* energy_dev, float* grad_dev, void* stream) {
+mreg_status mreg_unroll_grad_checkpointed(mreg_handle* h, const float* u0_dev, int32_t n_iters,
+                                          int32_t checkpoint_every, double* energy_dev,
+                                          float* grad_dev, void* stream) {
   if (!h || !u0_dev) return fail(MREG_ERR_INVALID_ARG, "handle or u0 is NULL");
   if (h->form != mreg::kFormExplicit || h->grad != MREG_GRAD_SPLINE)
     return fail(MREG_ERR_INVALID_ARG,
                 "the unrolled gradient needs the explicit mode with the spline gradient");
   if (n_iters < 0 || n_iters > 100000) return fail(MREG_ERR_INVALID_ARG, "n_iters out of range");
+  if (checkpoint_every < 0) return fail(MREG_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
   if (h->device_failed)
     return fail(MREG_ERR_DEVICE_CHECK, "an earlier launch gave up at a grid barrier; reset first");
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  // states u_0 .. u_{K-1} densely (K x nV float2), then three vectors
+  // segments of c iterations: the starting state of each is kept
+  // (checkpoints), the states inside one segment at a time (dense); c = K
+  // keeps every state in one segment and needs no recomputation
+  const int K = n_iters;
+  const int c = (checkpoint_every <= 0 || checkpoint_every >= K) ? std::max(K, 1) : checkpoint_every;
+  const int n_seg = K > 0 ? (K + c - 1) / c : 0;
+  const bool dense_only = n_seg <= 1;
   const size_t vec = align_up(sizeof(float2) * h->nV);
-  const size_t states = align_up(sizeof(float2) * h->nV * (size_t)n_iters);
-  const size_t need = states + 3 * vec;
+  const size_t dense = align_up(sizeof(float2) * h->nV * (size_t)c);
+  const size_t ckpts = dense_only ? 0 : align_up(sizeof(float2) * h->nV * (size_t)n_seg);
+  const size_t need = dense + ckpts + (dense_only ? 3 : 4) * vec;
   if (need > h->unroll_bytes) {
     CK(cudaStreamSynchronize(s), "synchronize");
     h->mem.put(h->unroll_buf, stream);
@@ -918,18 +927,29 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
     h->unroll_bytes = need;
   }
   char* base = (char*)h->unroll_buf;
-  float2* const ustates = (float2*)base;
-  float2* va = (float2*)(base + states);
-  float2* vb = (float2*)(base + states + vec);
-  float2* vc = (float2*)(base + states + 2 * vec);
-  // forward: u_0 .. u_{K-1} kept.  The iteration kernel stores each
-  // iteration's starting state itself (one launch per 1024 iterations).
-  CK(cudaMemcpyAsync(h->u, u0_dev, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s), "copy u0");
-  if (n_iters > 0) {
+  float2* const ustates = (float2*)base;                 // c states of one segment
+  float2* const ckpt = (float2*)(base + dense);          // n_seg segment starts
+  float2* va = (float2*)(base + dense + ckpts);
+  float2* vb = (float2*)(base + dense + ckpts + vec);
+  float2* vc = (float2*)(base + dense + ckpts + 2 * vec);
+  float2* const ukeep = (float2*)(base + dense + ckpts + 3 * vec);   // u_K (segmented runs)
+  const size_t ubytes = sizeof(float2) * h->nV;
+  // forward.  One segment: the iteration kernel stores each iteration's
+  // starting state itself (one launch per 1024 iterations).  Several: each
+  // segment's starting state is copied out before its launch.
+  CK(cudaMemcpyAsync(h->u, u0_dev, ubytes, cudaMemcpyDeviceToDevice, s), "copy u0");
+  if (dense_only && K > 0) {
     h->u_keep = ustates;
-    const mreg_status st = mreg_step(h, n_iters, stream);
+    const mreg_status st = mreg_step(h, K, stream);
     h->u_keep = nullptr;
     if (st) return st;
+  } else {
+    for (int g = 0; g < n_seg; ++g) {
+      CK(cudaMemcpyAsync(ckpt + (size_t)g * h->nV, h->u, ubytes, cudaMemcpyDeviceToDevice, s),
+         "checkpoint");
+      const mreg_status st = mreg_step(h, std::min(c, K - g * c), stream);
+      if (st) return st;
+    }
   }
   mreg_status st = mreg_warp_energy_grad(h, (const float*)h->u, energy_dev,
                                          grad_dev ? (float*)va : nullptr, stream);
@@ -948,16 +968,38 @@ mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iter
   a.cTeh = h->cTeh;
   a.ReV = h->ReV;
   const int passes = h->opts.smooth_passes > 0 ? h->opts.smooth_passes : 1;
-  CK(mreg::launch_unroll_adjoint(a, ustates, n_iters, passes, va, vb, vc, h->bar, h->status,
-                                 h->num_sms, s),
-     "adjoint launch");
-  for (int k = n_iters - 1; k >= 0; --k) {   // the kernel's rotation of the buffers
-    for (int p = 1; p < passes; ++p) std::swap(va, vc);
-    std::swap(va, vb);
+  if (!dense_only)
+    CK(cudaMemcpyAsync(ukeep, h->u, ubytes, cudaMemcpyDeviceToDevice, s), "keep u_K");
+  // backward, last segment first: recompute the segment's states from its
+  // checkpoint (the same kernel and launch shape, so bitwise the states of
+  // the forward run), then run the adjoint recursion over them
+  for (int g = n_seg - 1; g >= 0; --g) {
+    const int len = std::min(c, K - g * c);
+    if (!dense_only) {
+      CK(cudaMemcpyAsync(h->u, ckpt + (size_t)g * h->nV, ubytes, cudaMemcpyDeviceToDevice, s),
+         "restore checkpoint");
+      h->u_keep = ustates;
+      st = mreg_step(h, len, stream);
+      h->u_keep = nullptr;
+      if (st) return st;
+    }
+    CK(mreg::launch_unroll_adjoint(a, ustates, len, passes, va, vb, vc, h->bar, h->status,
+                                   h->num_sms, s),
+       "adjoint launch");
+    for (int k = len - 1; k >= 0; --k) {   // the kernel's rotation of the buffers
+      for (int p = 1; p < passes; ++p) std::swap(va, vc);
+      std::swap(va, vb);
+    }
   }
-  CK(cudaMemcpyAsync(grad_dev, va, sizeof(float2) * h->nV, cudaMemcpyDeviceToDevice, s),
-     "copy gradient");
+  if (!dense_only)
+    CK(cudaMemcpyAsync(h->u, ukeep, ubytes, cudaMemcpyDeviceToDevice, s), "restore u_K");
+  CK(cudaMemcpyAsync(grad_dev, va, ubytes, cudaMemcpyDeviceToDevice, s), "copy gradient");
   return MREG_OK;
+}
+
+mreg_status mreg_unroll_grad(mreg_handle* h, const float* u0_dev, int32_t n_iters,
+                             double* energy_dev, float* grad_dev, void* stream) {
+  return mreg_unroll_grad_checkpointed(h, u0_dev, n_iters, 0, energy_dev, grad_dev, stream);
 }
 
 mreg_status mreg_warp(mreg_handle* h, float* out_dev, double* msd_dev, void* stream) {

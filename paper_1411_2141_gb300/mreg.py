@@ -109,6 +109,7 @@ EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mr
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
            "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
            "mreg_test_barrier_timeout", "mreg_apply_operator", "mreg_batch_apply_operator",
+           "mreg_unroll_grad_checkpointed",
            "mreg_batch_create", "mreg_batch_run", "mreg_batch_tune",
            "mreg_batch_shape", "mreg_batch_iterate_ms", "mreg_batch_msd", "mreg_batch_get_field",
            "mreg_batch_stats", "mreg_batch_destroy"]
@@ -155,6 +156,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_prefilter_noalloc": ([vp, i64, vp, i32, i32, vp], i32),
         "mreg_warp_energy_grad": ([vp, vp, vp, vp, vp], i32),
         "mreg_unroll_grad": ([vp, vp, i32, vp, vp, vp], i32),
+        "mreg_unroll_grad_checkpointed": ([vp, vp, i32, i32, vp, vp, vp], i32),
         "mreg_test_barrier_timeout": ([vp, i32, i32, i64], i32),
         "mreg_apply_operator": ([vp, vp, vp, vp], i32),
         "mreg_batch_apply_operator": ([vp, vp, vp, vp], i32),
@@ -401,18 +403,22 @@ class Registration:
         _check(load().mreg_warp_energy_grad(self._h, u.data_ptr(), pe, pg, _stream_ptr(stream)),
                "mreg_warp_energy_grad")
 
-    def unroll_grad(self, u0, n_iters: int, energy=None, grad=None, stream=None):
+    def unroll_grad(self, u0, n_iters: int, energy=None, grad=None, stream=None,
+                    checkpoint_every: int = 0):
         """Asynchronous E(u_K) after n_iters iterations from ``u0`` into
         ``energy`` and dE(u_K)/du0 into ``grad`` (device tensors, either may
         be None); explicit mode with the spline gradient only.  The handle's
-        iterate is left at u_K."""
+        iterate is left at u_K.  checkpoint_every > 0 keeps only every
+        c-th state and recomputes the segments (bitwise the same result)."""
         if not _is_torch_cuda(u0) or str(u0.dtype) != "torch.float32" or not u0.is_contiguous() \
                 or tuple(u0.shape) != (self.n_nodes, 2):
             raise ValueError("u0 must be a contiguous (n_nodes, 2) float32 device tensor")
         pe = energy.data_ptr() if energy is not None else None
         pg = grad.data_ptr() if grad is not None else None
-        _check(load().mreg_unroll_grad(self._h, u0.data_ptr(), int(n_iters), pe, pg,
-                                       _stream_ptr(stream)), "mreg_unroll_grad")
+        _check(load().mreg_unroll_grad_checkpointed(self._h, u0.data_ptr(), int(n_iters),
+                                                    int(checkpoint_every), pe, pg,
+                                                    _stream_ptr(stream)),
+               "mreg_unroll_grad_checkpointed")
 
     def msd(self, stream=None) -> float:
         v = C.c_double()

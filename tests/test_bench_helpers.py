@@ -94,6 +94,8 @@ def test_launch_counts_match_the_measured_launch_lists():
     assert bench.launches_per_registration(args, 1100) == 14            # two 1024-iteration launches
     assert bench.launches_per_registration(types.SimpleNamespace(coeff="bf16"), 200) == 13
     assert bench.ADJOINT_LAUNCHES == 7
+    assert bench.adjoint_launches(20, 0) == 7 and bench.adjoint_launches(20, 20) == 7
+    assert bench.adjoint_launches(20, 5) == 4 + 5 * 4     # 4 segments
 
 
 def test_operator_bytes():

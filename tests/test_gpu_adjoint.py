@@ -153,8 +153,8 @@ def test_unrolled_gradient_config0(mreg, case0):
 
 
 def test_unrolled_gradient_256px_pairs(mreg):
-    """The checkpointed 20-iteration unroll on two of the 64 differentiation
-    pairs (256x256, ~5k nodes)."""
+    """The 20-iteration unroll on two of the 64 differentiation pairs
+    (256x256, ~5k nodes)."""
     specs = inputs.batched_specs(4)
     for spec in (specs[0], specs[33]):
         case = inputs.make_case(spec)
@@ -203,3 +203,35 @@ def test_unroll_of_zero_iterations_is_the_warp_gradient(mreg, case0):
         torch.cuda.synchronize()
         assert torch.equal(g0, g1) and torch.equal(E0, E1)
         assert np.abs(r.get_u() - u0.cpu().numpy()).max() == 0.0   # the iterate is u0
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+def test_checkpointed_unroll_is_bitwise_the_dense_one(mreg, passes):
+    """Keeping only every c-th state and recomputing the segments in the
+    backward pass gives the gradient, the energy and the final iterate of
+    the run that keeps every state, bit for bit (the segments are recomputed
+    by the same kernel in the same launch shape), for segment lengths that
+    divide K, that do not, of one iteration, and K itself."""
+    from paper_1411_2141_gb300.autograd import unrolled_warp_energy
+    case = inputs.make_case(inputs.batched_specs(4)[5])
+    K = case.spec.n_iter
+    u0 = torch.from_numpy(_smooth_u(case, 1.0, 21)).cuda()
+    with mreg.Registration(case.V, case.T, case.Re, case.Te, case.spec.alpha, case.spec.tau,
+                           mode="S0", grad="G1", smooth_passes=passes) as r:
+        def run(c):
+            E = torch.empty(1, dtype=torch.float64, device="cuda")
+            g = torch.empty_like(u0)
+            r.unroll_grad(u0, K, E, g, checkpoint_every=c)
+            torch.cuda.synchronize()
+            return E.cpu(), g.cpu(), r.get_u()
+        E0, g0, u0K = run(0)
+        for c in (1, 3, 5, 7, K):
+            E, g, uK = run(c)
+            assert torch.equal(E, E0) and torch.equal(g, g0), c
+            assert np.array_equal(uK, u0K), c
+        u = u0.clone().requires_grad_(True)
+        Ea = unrolled_warp_energy(u, r, K, 4)
+        Ea.backward()
+        assert torch.equal(u.grad.cpu(), g0) and float(Ea) == float(E0)
+        with pytest.raises(mreg.MregError):
+            r.unroll_grad(u0, K, None, torch.empty_like(u0), checkpoint_every=-1)
