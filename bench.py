@@ -107,8 +107,9 @@ def algorithmic_bytes_per_iteration(n_v: int, n_t: int, nnz: int, mode: str, cg_
         return sample + force + update
     graph = 4 * (n_v + 1) + 4 * nnz
     if mode == "S1" and solver == "chebyshev":
-        # first phase: graph, x in; b out, previous b in (verification); d, x' out; 1/diag(A)
-        first = graph + 8 * n_v + 16 * n_v + 16 * n_v + 8 * n_v + 8 * n_v + 4 * n_v
+        # first phase: graph, x in; b out, previous b in (verification); d, x' out;
+        # 1/diag(A); the previous iterate in and this one out (extrapolated guess)
+        first = graph + 8 * n_v + 16 * n_v + 16 * n_v + 8 * n_v + 8 * n_v + 4 * n_v + 16 * n_v
         # each further step: graph, x and b in, d in and out, 1/diag(A), x' out
         step = graph + 8 * n_v + 16 * n_v + 16 * n_v + 4 * n_v + 8 * n_v
         return sample + force + first + max(cg_its - 1.0, 0.0) * step

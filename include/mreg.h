@@ -105,7 +105,11 @@ enum {
  *       [-1, 1]); no inner products inside the solve.  The step count comes
  *       from the a-priori Chebyshev bound and ||r_0|| / ||b||, and every
  *       solve's true residual is verified against pcg_rtol (a solve that
- *       misses it is continued).                                           */
+ *       misses it is continued).  Each solve starts from the iterate
+ *       extrapolated from the last two, 2 u_k - u_{k-1} (u_k alone for the
+ *       first iteration after create, reset or set_u): the handle keeps
+ *       u_{k-1} across mreg_step calls (MREG_FIELD_U_PREV, mreg_set_u_prev),
+ *       so n steps in one call and in several calls give the same u.      */
 enum {
   MREG_SOLVER_AUTO = 0,
   MREG_SOLVER_CG = 1,
@@ -263,10 +267,15 @@ enum {
   MREG_FIELD_PCG_RESID = 9,  /* n double: final relative residual of each
                                 solve of the last mreg_step call (as
                                 mreg_stats_t.last_rel_resid)                  */
-  MREG_FIELD_COEF_TE_16 = 10 /* H x W uint16: the 16-bit copy of Te's
+  MREG_FIELD_COEF_TE_16 = 10,/* H x W uint16: the 16-bit copy of Te's
                                 coefficients (BF16 or FP16 bit patterns, as
                                 coeff_storage says); 0 elements with FP32
                                 storage                                       */
+  MREG_FIELD_U_PREV = 11     /* n_nodes x 2 float: the iterate one iteration
+                                before u, from which the Chebyshev solve
+                                extrapolates its next starting guess; 0
+                                elements when none is held (other solvers,
+                                or no iteration since create, reset, set_u) */
 };
 
 /* Fill *opts with the defaults listed in mreg_options. */
@@ -381,6 +390,16 @@ mreg_status mreg_energy_terms(mreg_handle* h, double* data_host, double* smooth_
  * sources and rejects non-finite host values (NONFINITE).                   */
 mreg_status mreg_get_u(mreg_handle* h, float* dst, int32_t dst_on_device, void* stream);
 mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, void* stream);
+
+/* Give the Chebyshev solve (S1) the iterate one iteration before u, so that
+ * a registration resumed from a checkpoint of u and MREG_FIELD_U_PREV
+ * continues bit for bit as the uninterrupted one; call it after set_u
+ * (which drops the held one).  src (n_nodes x 2 float, host or device as
+ * src_on_device says) is copied; NULL drops the held iterate.  Errors:
+ * INVALID_ARG for a handle whose solver is not the Chebyshev one,
+ * NONFINITE for a non-finite host value.  Asynchronous for device sources. */
+mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t src_on_device,
+                            void* stream);
 
 /* Copy one of the MREG_FIELD_* arrays.  count_out (may be NULL) receives the
  * number of elements; dst may be NULL to query the count only.  Blocks when

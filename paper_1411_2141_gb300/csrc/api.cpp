@@ -267,6 +267,8 @@ struct mreg_handle {
   int grid = 0, block = 0, warp_grid = 0;
   int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
   bool cheb = false;   // S1 solved by Chebyshev semi-iteration
+  int prev_guess = 0;  // Chebyshev: 0, or 1 + the history buffer holding the
+                       // iterate one iteration before u (IterArgs::prev_guess)
   bool nsync = false;  // its steps use the neighbour synchronisation
   unsigned* nflags = nullptr;
   int *nbr_idx = nullptr, *nbr_cnt = nullptr;
@@ -320,6 +322,7 @@ struct mreg_handle {
   mreg::IterArgs iter_args(int n_iters, int it0) const {
     mreg::IterArgs a{};
     a.it0 = it0;
+    a.prev_guess = cheb ? prev_guess : 0;
     a.nV = nV;
     a.nE = nE;
     a.W = W;
@@ -533,6 +536,7 @@ mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
   h->iterations_done = 0;
   h->last_n_iters = 0;
   h->last_force_buf = 0;
+  h->prev_guess = 0;
   h->device_failed = false;
   h->stall_block = -1;
   h->stall_barrier = 0;
@@ -856,6 +860,9 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
                             (cudaStream_t)stream),
        "iteration kernel launch");
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
+    // the launch's last iteration saved its starting iterate, u_{k-1}, to
+    // history buffer (n - 1 + prev_guess) & 1
+    if (h->cheb) h->prev_guess = 1 + ((n - 1 + a.prev_guess) & 1);
   }
   h->iterations_done += n_iters;
   h->last_n_iters = n_iters;
@@ -1086,6 +1093,29 @@ mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, 
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
      "copy u");
   if (!src_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+  h->prev_guess = 0;   // the previous iterate belonged to the old u
+  return MREG_OK;
+}
+
+mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t src_on_device,
+                            void* stream) {
+  if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->cheb)
+    return fail(MREG_ERR_INVALID_ARG, "only the Chebyshev solve of S1 keeps a previous iterate");
+  if (!src) {
+    h->prev_guess = 0;
+    return MREG_OK;
+  }
+  CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  if (!src_on_device)
+    for (int i = 0; i < 2 * h->nV; ++i)
+      if (!std::isfinite(src[i])) return fail(MREG_ERR_NONFINITE, "u_prev[%d] is not finite", i / 2);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(mreg::cheb_history(h->cg, h->nV, 0), src, sizeof(float2) * h->nV,
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+     "copy u_prev");
+  if (!src_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+  h->prev_guess = 1;
   return MREG_OK;
 }
 
@@ -1112,6 +1142,10 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
       src = h->cTeh ? (const void*)h->cTeh : (const void*)h->cTe16;
       count = (h->cTe16 || h->cTeh) ? npx : 0;
       esize = 2;
+      break;
+    case MREG_FIELD_U_PREV:
+      src = h->prev_guess ? mreg::cheb_history(h->cg, h->nV, h->prev_guess - 1) : nullptr;
+      count = h->prev_guess ? 2 * (int64_t)h->nV : 0;
       break;
     default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
   }

@@ -43,6 +43,10 @@ struct IterArgs {
   // holding the spectrum of D^-1 A, acosh(theta / delta), and the factor of
   // the a-priori step count (sqrt(max / min of diag A) over a safety margin)
   float cheb_theta, cheb_delta, cheb_acosh, cheb_scale;
+  // S1 by Chebyshev semi-iteration: 0 when no earlier iterate is held, else
+  // 1 + the history buffer (cheb_history) holding the iterate one iteration
+  // before u, from which the first solve of the launch extrapolates its guess
+  int prev_guess;
   float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
   // read-only mesh / operator data
   const float2* V;
@@ -76,7 +80,8 @@ struct IterArgs {
   float2* hq;            // edge form: per-edge force contribution
   float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s};
                          // the Chebyshev solve keeps its own state in the same
-                         // memory (b: 2 x nV float4, x: 2 x nV float2, d: nV float2)
+                         // memory (b: 2 x nV float4, x: 2 x nV float2, d: nV float2,
+                         // history: 2 x nV float2)
   float2* rt;            // true residual (FP32 copy) for restarts
   float4* b;             // right-hand side, float-float {x.hi, x.lo, y.hi, y.lo}
   // reductions / control
@@ -100,6 +105,14 @@ struct IterArgs {
   double* last;          // [0] last energy, [1] last rel. residual, [2] last CG its,
                          // [3] max CG its, [4] not-converged count
 };
+
+// The Chebyshev solve's two history buffers (nV float2 each) in the CG state
+// memory, after its right-hand sides (2 x nV float4) and x, x', d (3 x nV
+// float2): buffer b holds the iterate at the force phase of the iterations of
+// one parity, which the next iteration extrapolates its starting guess from.
+__host__ __device__ inline float2* cheb_history(float4* cg, int nV, int b) {
+  return reinterpret_cast<float2*>(cg + 2 * (size_t)nV) + (3 + (size_t)b) * nV;
+}
 
 struct WarpArgs {
   int W, H, nT;

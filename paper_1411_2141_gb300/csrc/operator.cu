@@ -13,10 +13,12 @@
 // that many loads are in flight together.  Measured on GB300 over the
 // 256-pair batch (2.0M nodes, 88 MB per product, L2 flushed): 33.8 us; one
 // row per thread, eight-entry gathers, four rows per thread and persistent
-// grids all took 34-42 us -- the product is bound by the latency of the
-// dependent row-pointer -> column -> x chain, not by loads in flight.  Nodes are in the mesh
-// generator's Morton order, so the gathered x of a warp stay in few cache
-// lines.  FP32 with fused multiply-adds; every sum runs in ascending
+// grids all took 34-42 us, and a warp-cooperative form (a warp's rows'
+// column indices read as one coalesced stretch, rows reduced by shuffles)
+// 44 us -- the product is bound by the latency of the dependent
+// row-pointer -> column -> x chain, not by loads in flight.  Nodes are in
+// the mesh generator's Morton order, so the gathered x of a warp stay in few
+// cache lines.  FP32 with fused multiply-adds; every sum runs in ascending
 // column order, so results are bitwise repeatable.
 #include <algorithm>
 

@@ -52,6 +52,7 @@ MREG_FIELD_ENERGY = 7
 MREG_FIELD_PCG_ITERS = 8
 MREG_FIELD_PCG_RESID = 9
 MREG_FIELD_COEF_TE_16 = 10
+MREG_FIELD_U_PREV = 11
 
 MODES = {"S0": MREG_MODE_EXPLICIT, "S1": MREG_MODE_UMBRELLA_IMPLICIT, "S2": MREG_MODE_FEM_IMPLICIT}
 GRADS = {"G0": MREG_GRAD_MESH, "G1": MREG_GRAD_SPLINE}
@@ -105,7 +106,8 @@ class mreg_stats_t(C.Structure):
 
 
 EXPORTS = ["mreg_default_options", "mreg_create", "mreg_reset", "mreg_step", "mreg_warp",
-           "mreg_msd", "mreg_energy", "mreg_energy_terms", "mreg_get_u", "mreg_set_u", "mreg_get_field",
+           "mreg_msd", "mreg_energy", "mreg_energy_terms", "mreg_get_u", "mreg_set_u",
+           "mreg_set_u_prev", "mreg_get_field",
            "mreg_stats", "mreg_destroy", "mreg_last_error", "mreg_version",
            "mreg_prefilter_noalloc", "mreg_warp_energy_grad", "mreg_unroll_grad",
            "mreg_test_barrier_timeout", "mreg_apply_operator", "mreg_batch_apply_operator",
@@ -148,6 +150,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_energy_terms": ([vp, C.POINTER(dbl), C.POINTER(dbl), vp], i32),
         "mreg_get_u": ([vp, vp, i32, vp], i32),
         "mreg_set_u": ([vp, vp, i32, vp], i32),
+        "mreg_set_u_prev": ([vp, vp, i32, vp], i32),
         "mreg_get_field": ([vp, i32, vp, i32, C.POINTER(i64), vp], i32),
         "mreg_stats": ([vp, C.POINTER(mreg_stats_t), vp], i32),
         "mreg_destroy": ([vp], None),
@@ -455,6 +458,22 @@ class Registration:
             raise ValueError("u must be (n_nodes, 2)")
         _check(load().mreg_set_u(self._h, a.ctypes.data, 0, _stream_ptr(stream)), "mreg_set_u")
 
+    def set_u_prev(self, u_prev, stream=None):
+        """The iterate one iteration before u for the Chebyshev solve's
+        extrapolated guess (None drops it); call after set_u."""
+        if u_prev is None:
+            _check(load().mreg_set_u_prev(self._h, None, 0, _stream_ptr(stream)), "mreg_set_u_prev")
+            return
+        if _is_torch_cuda(u_prev):
+            _check(load().mreg_set_u_prev(self._h, u_prev.data_ptr(), 1, _stream_ptr(stream)),
+                   "mreg_set_u_prev")
+            return
+        a = np.ascontiguousarray(u_prev, dtype=np.float32)
+        if a.shape != (self.n_nodes, 2):
+            raise ValueError("u_prev must be (n_nodes, 2)")
+        _check(load().mreg_set_u_prev(self._h, a.ctypes.data, 0, _stream_ptr(stream)),
+               "mreg_set_u_prev")
+
     def get_field(self, field: int, stream=None) -> np.ndarray:
         lib = load()
         n = C.c_int64()
@@ -467,7 +486,7 @@ class Registration:
         if n.value:
             _check(lib.mreg_get_field(self._h, field, out.ctypes.data, 0, None, _stream_ptr(stream)),
                    "mreg_get_field")
-        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE, MREG_FIELD_U_PREV):
             out = out.reshape(-1, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
                 field == MREG_FIELD_COEF_TE_16 and n.value):
@@ -607,7 +626,7 @@ class Batch:
         if n.value:
             _check(lib.mreg_batch_get_field(self._h, int(pair), field, out.ctypes.data, 0, None,
                                             _stream_ptr(stream)), "mreg_batch_get_field")
-        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE, MREG_FIELD_U_PREV):
             out = out.reshape(-1, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
                 field == MREG_FIELD_COEF_TE_16 and n.value):
