@@ -49,7 +49,7 @@ constexpr int kSetupWarps = 4;
 // DIR 0: rows of Re and Te into tmp; DIR 1: columns of tmp into the
 // coefficients.  Warps [0, tasks) work on Re, [tasks, 2 tasks) on Te.
 template <int DIR>
-__global__ void __launch_bounds__(32 * kSetupWarps) k_batch_prefilter(const BatchSetupArgs a) {
+__global__ void __launch_bounds__(32 * kSetupWarps, 4) k_batch_prefilter(const BatchSetupArgs a) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * kSetupWarps + warp;
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(32 * kSetupWarps) k_batch_prefilter(const Batc
     in = img ? ps.tmpT : ps.tmpR;
     out = img ? ps.cTe : ps.cRe;
   }
-  prefilter_task<DIR>(in, ps.W, out, ps.W, ps.W, ps.H, t, smem + (size_t)warp * kWin * kPitch);
+  prefilter_task<DIR>(in, ps.W, out, ps.W, ps.W, ps.H, t,
+                      smem + warp * prefilter_smem_per_warp<DIR>() / sizeof(float));
 }
 
 __global__ void k_batch_sample_nodes(const BatchSetupArgs a) {
@@ -292,12 +293,9 @@ int grid_for(int64_t n, int block) {
 // Function attributes are set here, outside any stream capture; the
 // launchers below only enqueue work (they may be recorded into a graph).
 cudaError_t batch_prepare(int form, int grad, int block, int minb, bool cheb) {
-  const size_t smem = kSmemPerWarp * kSetupWarps;
+  const size_t smem = prefilter_smem_per_warp<0>() * kSetupWarps;
   cudaError_t e = cudaFuncSetAttribute(k_batch_prefilter<0>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch_prefilter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
   if (e != cudaSuccess) return e;
   void* k = select_batch_kernel(form, grad, minb, cheb);
   if (!k) return cudaErrorInvalidValue;
@@ -306,13 +304,13 @@ cudaError_t batch_prepare(int form, int grad, int block, int minb, bool cheb) {
 }
 
 cudaError_t batch_setup(const BatchSetupArgs& a, bool edges, cudaStream_t s) {
-  const size_t smem = kSmemPerWarp * kSetupWarps;
+  const size_t smem = prefilter_smem_per_warp<0>() * kSetupWarps;
   if (a.tasks[0] > 0)
     k_batch_prefilter<0><<<(2 * a.tasks[0] + kSetupWarps - 1) / kSetupWarps, 32 * kSetupWarps,
                            smem, s>>>(a);
   if (a.tasks[1] > 0)
     k_batch_prefilter<1><<<(2 * a.tasks[1] + kSetupWarps - 1) / kSetupWarps, 32 * kSetupWarps,
-                           smem, s>>>(a);
+                           0, s>>>(a);
   if (a.nodes > 0) k_batch_sample_nodes<<<grid_for(a.nodes, 256), 256, 0, s>>>(a);
   if (edges && a.edges > 0) k_batch_sample_edges<<<grid_for(a.edges, 256), 256, 0, s>>>(a);
   return cudaGetLastError();

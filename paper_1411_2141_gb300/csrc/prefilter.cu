@@ -8,16 +8,18 @@
 namespace mreg {
 namespace {
 
-// DIR 0: rows, DIR 1: columns; one warp per task.
+// DIR 0: rows, DIR 1: columns; one warp per task (a window of 96 floats in
+// registers per lane: at most 128 registers, four blocks per SM).
 template <int DIR>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
 k_prefilter(const float* __restrict__ in, int64_t in_stride, float* __restrict__ out,
             int64_t out_stride, int W, int H) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   if (gw >= prefilter_tasks<DIR>(W, H)) return;   // warp-uniform; no block barrier below
-  prefilter_task<DIR>(in, in_stride, out, out_stride, W, H, gw, smem + (size_t)warp * kWin * kPitch);
+  prefilter_task<DIR>(in, in_stride, out, out_stride, W, H, gw,
+                      smem + warp * prefilter_smem_per_warp<DIR>() / sizeof(float));
 }
 
 // Re (or any coefficient image) sampled at the undeformed nodes.
@@ -118,18 +120,16 @@ cudaError_t launch_to_fp16(const float* src, int64_t n, __half* dst, cudaStream_
 
 cudaError_t launch_prefilter(const float* img, int64_t stride, float* tmp, float* coef, int W,
                              int H, cudaStream_t s) {
-  const size_t smem = kSmemPerWarp * kWarpsPerBlock;
+  const size_t smem_r = prefilter_smem_per_warp<0>() * kWarpsPerBlock;
   // the attribute is per device; setting it is cheap, so set it every time
   cudaError_t e = cudaFuncSetAttribute(k_prefilter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_prefilter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                       (int)smem_r);
   if (e != cudaSuccess) return e;
   const int warps_r = prefilter_tasks<0>(W, H);
   const int warps_c = prefilter_tasks<1>(W, H);
-  k_prefilter<0><<<(warps_r + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem, s>>>(
-      img, stride, tmp, W, W, H);
-  k_prefilter<1><<<(warps_c + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem, s>>>(
+  k_prefilter<0><<<(warps_r + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_r,
+                   s>>>(img, stride, tmp, W, W, H);
+  k_prefilter<1><<<(warps_c + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, 0, s>>>(
       tmp, W, coef, W, W, H);
   return cudaGetLastError();
 }

@@ -9,14 +9,17 @@
 // One warp filters 32 lines (rows, then columns) over one segment of kSegLen
 // outputs.  The causal recursion c+(n) = 6 s(n) + z1 c+(n-1) and the
 // anticausal recursion c-(n) = z1 (c-(n+1) - c+(n)) run lane-per-line over a
-// window staged in shared memory.  The window extends kWarm samples beyond
-// the segment on each side: the state entering the window is taken as 0,
-// whose effect decays as |z1|^kWarm ~ 1.9e-14, far below FP32 resolution.
-// Where the window reaches the image border the exact mirror-boundary
-// initial values are used instead, so every line matches the full-length
-// recursion.  Windows are staged transposed (line-major in the lane index)
-// so that both the global loads/stores and the lane-per-line shared-memory
-// accesses are conflict-free.
+// window of the line's mirror-symmetric extension held in registers, which
+// extends kWarm samples beyond the segment on each side: the states
+// entering the window are taken as 0, whose effect decays as
+// |z1|^kWarm ~ 7e-10, below FP32 resolution.  Reading the mirror extension
+// at the image border makes the windowed recursion the mirror-boundary
+// prefilter itself (Unser's exact initial values are the infinite
+// recursions over that extension), so every window is handled alike.  All
+// of a lane's window loads are independent and issued together.  Columns
+// are read directly (consecutive lanes, consecutive addresses); rows are
+// staged transposed through shared memory so that the global loads and
+// stores stay warp-wide and the lane-per-line accesses conflict-free.
 //
 // Pixel map (set-up of step a4): every pixel centre gets the smallest-index
 // closed triangle of the undeformed mesh that contains it.  The inside test
@@ -32,38 +35,44 @@
 namespace mreg {
 namespace {
 
-constexpr int kSegLen = 64;
-constexpr int kWarm = 24;
-constexpr int kWin = kSegLen + 2 * kWarm;
-constexpr int kPitch = 33;                 // 32 lines + 1 pad word
+constexpr int kSegLen = 64;                  // outputs of a line per task
+constexpr int kWarm = 16;                    // warm-up samples on each side
+constexpr int kWin = kSegLen + 2 * kWarm;    // window of a line, held in registers
+constexpr int kPitch = 33;                   // row-pass staging: 32 lines + 1 pad word
 constexpr int kWarpsPerBlock = 4;
-constexpr size_t kSmemPerWarp = (size_t)kWin * kPitch * sizeof(float);
-static_assert(kWin <= 4 * 32, "the row-pass staging loads at most 4 x 32 samples per line");
+static_assert(kWin % 32 == 0, "the row pass stages a window in whole warp-wide loads");
 
+// Shared memory per warp: the row pass stages its window transposed; the
+// column pass reads its lines directly (consecutive lanes, consecutive
+// columns) and needs none.
+template <int DIR>
+__host__ __device__ constexpr size_t prefilter_smem_per_warp() {
+  return DIR == 0 ? (size_t)kWin * kPitch * sizeof(float) : 0;
+}
 
-// Exact causal initial value c+(0) = sum_k z1^k c~(k) over the mirror-periodic
-// extension (period 2N-2), for short lines; the forward sum truncated after
-// kWarm terms otherwise (error |z1|^kWarm).  t: line in shared memory with
-// stride kPitch, already multiplied by the gain.
-__device__ float causal_init(const float* t, int N) {
+// Index j of the mirror-symmetric extension of a line of N >= 2 samples
+// (s(-j) = s(j), s(N-1+j) = s(N-1-j), period 2N-2) folded into [0, N).
+__device__ __forceinline__ int mirror_index(int j, int N) {
+  if ((unsigned)j < (unsigned)N) return j;
+  const int p = 2 * N - 2;
+  j %= p;
+  if (j < 0) j += p;
+  return j < N ? j : p - j;
+}
+
+// The two recursions over one window held in registers, v = gain * samples:
+// causal c+(k) = v(k) + z1 c+(k-1) from a zero state before the window,
+// then anticausal c(k) = z1 (c(k+1) - c+(k)) from a zero state after it,
+// down to the first output (kWarm).  The zero states stand in for the
+// line's samples beyond the window; their effect on the outputs decays as
+// |z1|^kWarm ~ 7e-10 (relative to the samples), below FP32 resolution.
+__device__ __forceinline__ void prefilter_window(float (&v)[kWin]) {
   const float z = kZ1;
-  if (N > kWarm) {
-    float acc = 0.0f, zk = 1.0f;
-    for (int k = 0; k < kWarm; ++k) {
-      acc += zk * t[k * kPitch];
-      zk *= z;
-    }
-    return acc;
-  }
-  // N <= kWarm: one full period, then the geometric factor.
-  const int period = 2 * N - 2;
-  float acc = 0.0f, zk = 1.0f;
-  for (int k = 0; k < period; ++k) {
-    const int j = k < N ? k : period - k;
-    acc += zk * t[j * kPitch];
-    zk *= z;
-  }
-  return acc / (1.0f - zk);   // zk == z^period here
+#pragma unroll
+  for (int k = 1; k < kWin; ++k) v[k] = __fmaf_rn(z, v[k - 1], v[k]);
+  v[kWin - 1] = -z * v[kWin - 1];
+#pragma unroll
+  for (int k = kWin - 2; k >= kWarm; --k) v[k] = z * (v[k + 1] - v[k]);
 }
 
 // Number of warp tasks (32 lines x one segment) of one pass.
@@ -74,8 +83,14 @@ __host__ __device__ __forceinline__ int prefilter_tasks(int W, int H) {
 }
 
 // One warp task gw < prefilter_tasks<DIR>(W, H) of a pass.  DIR 0: lines are
-// rows (recursion along x).  DIR 1: lines are columns.  tile: this warp's
-// kWin x kPitch floats of shared memory.  Called by all 32 lanes.
+// rows (recursion along x).  DIR 1: lines are columns.  Lane l filters line
+// line0 + l over the window [s0 - kWarm, s0 + kSegLen + kWarm) of its
+// mirror-extended samples and writes the segment [s0, s0 + kSegLen).  With
+// the mirror extension, the recursions need no special initial values at
+// the image border: the infinite causal/anticausal recursion over the
+// mirror-symmetric line is exactly the mirror-boundary B-spline prefilter.
+// tile: this warp's prefilter_smem_per_warp<DIR>() bytes of shared memory
+// (unused by DIR 1).  Called by all 32 lanes.
 template <int DIR>
 __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int64_t in_stride,
                                                float* __restrict__ out, int64_t out_stride, int W,
@@ -85,84 +100,62 @@ __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int
   const int nlines = DIR == 0 ? H : W;
   const int nseg = (N + kSegLen - 1) / kSegLen;
   const int line0 = (gw / nseg) * 32;
-  const int seg = gw % nseg;
-  const int s0 = seg * kSegLen, s1 = min(N, s0 + kSegLen);
-  const int w0 = max(0, s0 - kWarm), w1 = min(N, s1 + kWarm);
-  const int wn = w1 - w0;
+  const int s0 = (gw % nseg) * kSegLen;
+  const int w0 = s0 - kWarm;
   const int nl = min(32, nlines - line0);
+  const int on = min(kSegLen, N - s0);
   const float gain = 6.0f;
+  float v[kWin];
 
-  // stage the window: tile[k * kPitch + l] = gain * sample k of line l
   if (DIR == 0) {
-    // eight lines per round, every load of the round issued before the
-    // shared-memory stores (kWin <= 4 * 32 samples per line)
-    for (int l0 = 0; l0 < nl; l0 += 8) {
-      float v[8][4];
+    // stage: the loads of 16 lines (three warp-wide loads each) are issued
+    // before their transposed shared-memory stores
+    int col[kWin / 32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+    for (int j = 0; j < kWin / 32; ++j) col[j] = mirror_index(w0 + lane + 32 * j, N);
+#pragma unroll
+    for (int l0 = 0; l0 < 32; l0 += 16) {
+      float r[16][kWin / 32];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
         const int l = l0 + q;
-        const float* src = in + (int64_t)(line0 + (l < nl ? l : 0)) * in_stride + w0;
+        const float* src = in + (int64_t)(line0 + (l < nl ? l : 0)) * in_stride;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int k = lane + 32 * j;
-          v[q][j] = (l < nl && k < wn) ? src[k] : 0.0f;
-        }
+        for (int j = 0; j < kWin / 32; ++j) r[q][j] = l < nl ? __ldg(src + col[j]) : 0.0f;
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int l = l0 + q;
+      for (int q = 0; q < 16; ++q)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int k = lane + 32 * j;
-          if (l < nl && k < wn) tile[k * kPitch + l] = gain * v[q][j];
-        }
-      }
+        for (int j = 0; j < kWin / 32; ++j) tile[(lane + 32 * j) * kPitch + l0 + q] = gain * r[q][j];
     }
-  } else {
-    if (lane < nl) {
-      for (int k = 0; k < wn; ++k)
-        tile[k * kPitch + lane] = gain * in[(int64_t)(w0 + k) * in_stride + line0 + lane];
-    }
-  }
-  __syncwarp();
-
-  if (lane < nl) {
-    float* t = tile + lane;
-    const float z = kZ1;
-    // causal pass, in place
-    float cp = (w0 == 0) ? causal_init(t, N) : t[0];
-    t[0] = cp;
-    for (int k = 1; k < wn; ++k) {
-      cp = t[k * kPitch] + z * cp;
-      t[k * kPitch] = cp;
-    }
-    // anticausal pass, in place
-    float cm;
-    if (w1 == N) {
-      cm = (z / (z * z - 1.0f)) * (t[(wn - 1) * kPitch] + z * t[(wn - 2) * kPitch]);
-    } else {
-      cm = -z * t[(wn - 1) * kPitch];
-    }
-    t[(wn - 1) * kPitch] = cm;
-    for (int k = wn - 2; k >= 0; --k) {
-      cm = z * (cm - t[k * kPitch]);
-      t[k * kPitch] = cm;
-    }
-  }
-  __syncwarp();
-
-  // write the segment's outputs
-  const int o0 = s0 - w0, on = s1 - s0;
-  if (DIR == 0) {
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) v[k] = tile[k * kPitch + lane];
+    prefilter_window(v);
+    __syncwarp();   // every lane has read the window before outputs overwrite it
+#pragma unroll
+    for (int k = 0; k < kSegLen; ++k) tile[k * kPitch + lane] = v[kWarm + k];
+    __syncwarp();
+    // write the segment: each row's outputs as warp-wide stores
     for (int l = 0; l < nl; ++l) {
       float* dst = out + (int64_t)(line0 + l) * out_stride + s0;
-      for (int k = lane; k < on; k += 32) dst[k] = tile[(o0 + k) * kPitch + l];
+#pragma unroll
+      for (int j = 0; j < kSegLen / 32; ++j) {
+        const int k = lane + 32 * j;
+        if (k < on) dst[k] = tile[k * kPitch + l];
+      }
     }
   } else {
-    if (lane < nl) {
-      for (int k = 0; k < on; ++k)
-        out[(int64_t)(s0 + k) * out_stride + line0 + lane] = tile[(o0 + k) * kPitch + lane];
-    }
+    if (lane >= nl) return;   // no warp-wide operation follows
+    const float* src = in + line0 + lane;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k)
+      v[k] = gain * __ldg(src + (int64_t)mirror_index(w0 + k, N) * in_stride);
+    prefilter_window(v);
+    float* dst = out + (int64_t)s0 * out_stride + line0 + lane;
+#pragma unroll
+    for (int k = 0; k < kSegLen; ++k)
+      if (k < on) dst[(int64_t)k * out_stride] = v[kWarm + k];
   }
 }
 
