@@ -106,10 +106,11 @@ enum {
  *       from the a-priori Chebyshev bound and ||r_0|| / ||b||, and every
  *       solve's true residual is verified against pcg_rtol (a solve that
  *       misses it is continued).  Each solve starts from the iterate
- *       extrapolated from the last two, 2 u_k - u_{k-1} (u_k alone for the
- *       first iteration after create, reset or set_u): the handle keeps
- *       u_{k-1} across mreg_step calls (MREG_FIELD_U_PREV, mreg_set_u_prev),
- *       so n steps in one call and in several calls give the same u.      */
+ *       extrapolated from the last three, 3 (u_k - u_{k-1}) + u_{k-2}
+ *       (2 u_k - u_{k-1}, or u_k, while fewer are known: after create,
+ *       reset or set_u): the handle keeps u_{k-1} and u_{k-2} across
+ *       mreg_step calls (MREG_FIELD_U_PREV, mreg_set_u_prev), so n steps in
+ *       one call and in several calls give the same u.                    */
 enum {
   MREG_SOLVER_AUTO = 0,
   MREG_SOLVER_CG = 1,
@@ -271,11 +272,12 @@ enum {
                                 coefficients (BF16 or FP16 bit patterns, as
                                 coeff_storage says); 0 elements with FP32
                                 storage                                       */
-  MREG_FIELD_U_PREV = 11     /* n_nodes x 2 float: the iterate one iteration
-                                before u, from which the Chebyshev solve
-                                extrapolates its next starting guess; 0
-                                elements when none is held (other solvers,
-                                or no iteration since create, reset, set_u) */
+  MREG_FIELD_U_PREV = 11     /* n_prev x n_nodes x 2 float: the iterates one
+                                and two iterations before u (newest first),
+                                from which the Chebyshev solve extrapolates
+                                its next starting guess; n_prev = 0, 1 or 2
+                                as held (0 for other solvers; it restarts at
+                                0 with create, reset and set_u)              */
 };
 
 /* Fill *opts with the defaults listed in mreg_options. */
@@ -391,15 +393,17 @@ mreg_status mreg_energy_terms(mreg_handle* h, double* data_host, double* smooth_
 mreg_status mreg_get_u(mreg_handle* h, float* dst, int32_t dst_on_device, void* stream);
 mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, void* stream);
 
-/* Give the Chebyshev solve (S1) the iterate one iteration before u, so that
- * a registration resumed from a checkpoint of u and MREG_FIELD_U_PREV
- * continues bit for bit as the uninterrupted one; call it after set_u
- * (which drops the held one).  src (n_nodes x 2 float, host or device as
- * src_on_device says) is copied; NULL drops the held iterate.  Errors:
- * INVALID_ARG for a handle whose solver is not the Chebyshev one,
- * NONFINITE for a non-finite host value.  Asynchronous for device sources. */
-mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t src_on_device,
-                            void* stream);
+/* Give the Chebyshev solve (S1) the n_prev (0, 1 or 2) iterates before u,
+ * newest first (the layout of MREG_FIELD_U_PREV), so that a registration
+ * resumed from a checkpoint of u and MREG_FIELD_U_PREV continues bit for bit
+ * as the uninterrupted one; call it after set_u (which drops the held
+ * ones).  src (n_prev x n_nodes x 2 float, host or device as src_on_device
+ * says) is copied; n_prev = 0 drops the held iterates (src may be NULL).
+ * Errors: INVALID_ARG for a handle whose solver is not the Chebyshev one or
+ * an n_prev outside 0-2, NONFINITE for a non-finite host value.
+ * Asynchronous for device sources.                                         */
+mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t n_prev,
+                            int32_t src_on_device, void* stream);
 
 /* Copy one of the MREG_FIELD_* arrays.  count_out (may be NULL) receives the
  * number of elements; dst may be NULL to query the count only.  Blocks when

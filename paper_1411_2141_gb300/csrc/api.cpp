@@ -267,8 +267,8 @@ struct mreg_handle {
   int grid = 0, block = 0, warp_grid = 0;
   int minb = 1;   // iteration kernel variant: register budget for minb blocks per SM
   bool cheb = false;   // S1 solved by Chebyshev semi-iteration
-  int prev_guess = 0;  // Chebyshev: 0, or 1 + the history buffer holding the
-                       // iterate one iteration before u (IterArgs::prev_guess)
+  int hist_held = 0;   // Chebyshev: iterates before u held (IterArgs::hist_held)
+  int hist_pos = 0;    // and the history buffer the next iteration writes
   bool nsync = false;  // its steps use the neighbour synchronisation
   unsigned* nflags = nullptr;
   int *nbr_idx = nullptr, *nbr_cnt = nullptr;
@@ -322,7 +322,8 @@ struct mreg_handle {
   mreg::IterArgs iter_args(int n_iters, int it0) const {
     mreg::IterArgs a{};
     a.it0 = it0;
-    a.prev_guess = cheb ? prev_guess : 0;
+    a.hist_held = cheb ? hist_held : 0;
+    a.hist_pos = cheb ? hist_pos : 0;
     a.nV = nV;
     a.nE = nE;
     a.W = W;
@@ -420,7 +421,11 @@ mreg_status validate_image(const mreg_image* im, const char* name) {
 // widened by 1e-5 relative, far more than the FP32 rounding of the Jacobi
 // entries moves it (and so that l = 0 gives a non-empty interval).  The step
 // count uses the bound with sqrt(m_max / m_min) (the change from the
-// D^-1/2-weighted norm to the 2-norm) over a safety margin of 1/2.
+// D^-1/2-weighted norm to the 2-norm) and no further margin: the bound holds
+// in exact arithmetic and is far from tight in practice (an FP64 run of the
+// solves along the 512^2 pair's trajectory ends every solve below 0.43
+// rtol), which leaves room for the FP32 floor of the true residual
+// (~3e-8); every solve is verified anyway and continued if it misses rtol.
 void chebyshev_params(double lam, int m_min, int m_max, float out[4]) {
   const double lo = (1.0 / (1.0 + lam)) * (1.0 - 1e-5);
   const double hi = ((1.0 + 2.0 * lam) / (1.0 + lam)) * (1.0 + 1e-5);
@@ -428,7 +433,7 @@ void chebyshev_params(double lam, int m_min, int m_max, float out[4]) {
   out[0] = (float)theta;
   out[1] = (float)delta;
   out[2] = (float)std::acosh(theta / delta);
-  out[3] = (float)(std::sqrt((double)std::max(m_max, 1) / (double)std::max(m_min, 1)) / 0.5);
+  out[3] = (float)std::sqrt((double)std::max(m_max, 1) / (double)std::max(m_min, 1));
 }
 
 void valence_range(const int* ptr, int n, int* m_min, int* m_max) {
@@ -536,7 +541,8 @@ mreg_status device_setup(mreg_handle* h, cudaStream_t s, bool check_cover) {
   h->iterations_done = 0;
   h->last_n_iters = 0;
   h->last_force_buf = 0;
-  h->prev_guess = 0;
+  h->hist_held = 0;
+  h->hist_pos = 0;
   h->device_failed = false;
   h->stall_block = -1;
   h->stall_barrier = 0;
@@ -860,9 +866,12 @@ mreg_status mreg_step(mreg_handle* h, int32_t n_iters, void* stream) {
                             (cudaStream_t)stream),
        "iteration kernel launch");
     h->last_force_buf = (n - 1) & 1;   // F of a launch's last iteration
-    // the launch's last iteration saved its starting iterate, u_{k-1}, to
-    // history buffer (n - 1 + prev_guess) & 1
-    if (h->cheb) h->prev_guess = 1 + ((n - 1 + a.prev_guess) & 1);
+    // iteration j of the launch saved its starting iterate to history
+    // buffer (hist_pos + j) mod 3
+    if (h->cheb) {
+      h->hist_pos = (h->hist_pos + n) % 3;
+      h->hist_held = std::min(2, h->hist_held + n);
+    }
   }
   h->iterations_done += n_iters;
   h->last_n_iters = n_iters;
@@ -1093,29 +1102,37 @@ mreg_status mreg_set_u(mreg_handle* h, const float* src, int32_t src_on_device, 
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
      "copy u");
   if (!src_on_device) CK(cudaStreamSynchronize(s), "synchronize");
-  h->prev_guess = 0;   // the previous iterate belonged to the old u
+  h->hist_held = 0;   // the earlier iterates belonged to the old u
   return MREG_OK;
 }
 
-mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t src_on_device,
-                            void* stream) {
+mreg_status mreg_set_u_prev(mreg_handle* h, const float* src, int32_t n_prev,
+                            int32_t src_on_device, void* stream) {
   if (!h) return fail(MREG_ERR_INVALID_ARG, "handle is NULL");
   if (!h->cheb)
-    return fail(MREG_ERR_INVALID_ARG, "only the Chebyshev solve of S1 keeps a previous iterate");
-  if (!src) {
-    h->prev_guess = 0;
+    return fail(MREG_ERR_INVALID_ARG, "only the Chebyshev solve of S1 keeps earlier iterates");
+  if (n_prev < 0 || n_prev > 2) return fail(MREG_ERR_INVALID_ARG, "n_prev must be 0, 1 or 2");
+  if (n_prev == 0) {
+    h->hist_held = 0;
     return MREG_OK;
   }
+  if (!src) return fail(MREG_ERR_INVALID_ARG, "source is NULL");
   CK(cudaSetDevice(h->dev), "cudaSetDevice");
+  const int64_t n = 2 * (int64_t)h->nV;
   if (!src_on_device)
-    for (int i = 0; i < 2 * h->nV; ++i)
-      if (!std::isfinite(src[i])) return fail(MREG_ERR_NONFINITE, "u_prev[%d] is not finite", i / 2);
+    for (int64_t i = 0; i < n * n_prev; ++i)
+      if (!std::isfinite(src[i]))
+        return fail(MREG_ERR_NONFINITE, "u_prev[%d] is not finite", (int)(i / 2));
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(mreg::cheb_history(h->cg, h->nV, 0), src, sizeof(float2) * h->nV,
-                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
-     "copy u_prev");
+  // the ring restarts: u_{k-1} in buffer 2, u_{k-2} in buffer 1, buffer 0 next
+  for (int j = 0; j < n_prev; ++j)
+    CK(cudaMemcpyAsync(mreg::cheb_history(h->cg, h->nV, 2 - j), src + j * n,
+                       sizeof(float) * n,
+                       src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+       "copy u_prev");
   if (!src_on_device) CK(cudaStreamSynchronize(s), "synchronize");
-  h->prev_guess = 1;
+  h->hist_pos = 0;
+  h->hist_held = n_prev;
   return MREG_OK;
 }
 
@@ -1143,10 +1160,21 @@ mreg_status mreg_get_field(mreg_handle* h, int32_t field, void* dst, int32_t dst
       count = (h->cTe16 || h->cTeh) ? npx : 0;
       esize = 2;
       break;
-    case MREG_FIELD_U_PREV:
-      src = h->prev_guess ? mreg::cheb_history(h->cg, h->nV, h->prev_guess - 1) : nullptr;
-      count = h->prev_guess ? 2 * (int64_t)h->nV : 0;
-      break;
+    case MREG_FIELD_U_PREV: {   // newest first, from two buffers of the ring
+      const int64_t n = 2 * (int64_t)h->nV;
+      if (count_out) *count_out = h->hist_held * n;
+      if (!dst || h->hist_held == 0) return MREG_OK;
+      CK(cudaSetDevice(h->dev), "cudaSetDevice");
+      cudaStream_t s = (cudaStream_t)stream;
+      for (int j = 0; j < h->hist_held; ++j)
+        CK(cudaMemcpyAsync((float*)dst + j * n,
+                           mreg::cheb_history(h->cg, h->nV, (h->hist_pos + 2 - j) % 3),
+                           sizeof(float) * n,
+                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+           "copy field");
+      if (!dst_on_device) CK(cudaStreamSynchronize(s), "synchronize");
+      return MREG_OK;
+    }
     default: return fail(MREG_ERR_INVALID_ARG, "unknown field %d", field);
   }
   if (count_out) *count_out = count;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <limits>
 #include <atomic>
 #include <climits>
 #include <cmath>
@@ -70,8 +71,11 @@ struct mreg_batch {
   int* d_queue = nullptr;
   int64_t* d_px_off = nullptr;
   int* d_counts = nullptr;
-  int2* op_tiles = nullptr;   // (pair, first node) of the operator's blocks, on first use
-  int n_op_tiles = 0;
+  // the system matrices in sliced-ELLPACK form, built on the operator's first use
+  mreg::SellSlice* sell_slices = nullptr;
+  int* sell_col = nullptr;
+  float* sell_val = nullptr;
+  int n_sell_slices = 0;
   // launch shape and its scratch
   int team_ctas = 2, block = 256, minb = 1, n_teams = 0;
   float* part = nullptr;     // per team reduction records
@@ -232,23 +236,69 @@ mreg_status mreg_batch_apply_operator(mreg_batch* b, const float* x_dev, float* 
   if (x_dev == y_dev) return fail(MREG_ERR_INVALID_ARG, "x and y must not be the same buffer");
   CK(cudaSetDevice(b->dev), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  if (!b->op_tiles) {   // blocks of consecutive nodes, none straddling two pairs
-    const int per = mreg::operator_tile_nodes();
-    std::vector<int2> tiles;
-    for (int p = 0; p < b->n_pairs; ++p)
-      for (int i0 = 0; i0 < b->info[p].nV; i0 += per) tiles.push_back(make_int2(p, i0));
-    void* mem = nullptr;
-    const mreg_status st = b->mem.get(&mem, tiles.size() * sizeof(int2), stream);
-    if (st) return st;
-    CK(cudaMemcpyAsync(mem, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s),
-       "upload");
+  if (!b->sell_slices) {
+    // each pair's rows in slices of 32, from the CSR the batch holds: entry k
+    // of row r of a slice at col[off + 32 k + r] (packed node index, -1 past
+    // the row's end), its value (S2) at the same place of val
+    const bool fem = b->form != mreg::kFormUmbrella;
+    std::vector<mreg::SellSlice> sl;
+    std::vector<int> col;
+    std::vector<float> val;
+    std::vector<int> ptr, adj;
+    std::vector<float> off_val;
     CK(cudaStreamSynchronize(s), "synchronize");
-    b->op_tiles = (int2*)mem;
-    b->n_op_tiles = (int)tiles.size();
+    for (int p = 0; p < b->n_pairs; ++p) {
+      const PairInfo& I = b->info[p];
+      const mreg::IterArgs& a = b->h_args[p];
+      ptr.resize((size_t)I.nV + 1);
+      adj.resize((size_t)I.nnz);
+      CK(cudaMemcpy(ptr.data(), a.adj_ptr, ptr.size() * 4, cudaMemcpyDeviceToHost), "copy");
+      CK(cudaMemcpy(adj.data(), a.adj_col, adj.size() * 4, cudaMemcpyDeviceToHost), "copy");
+      if (fem) {
+        off_val.resize((size_t)I.nnz);
+        CK(cudaMemcpy(off_val.data(), a.Aoff, off_val.size() * 4, cudaMemcpyDeviceToHost), "copy");
+      }
+      for (int r0 = 0; r0 < I.nV; r0 += 32) {
+        const int rows = std::min(32, I.nV - r0);
+        int w = 0;
+        for (int r = 0; r < rows; ++r) w = std::max(w, ptr[r0 + r + 1] - ptr[r0 + r]);
+        const size_t base = col.size();
+        col.resize(base + 32 * (size_t)w, -1);
+        if (fem) val.resize(base + 32 * (size_t)w, 0.0f);
+        for (int r = 0; r < rows; ++r)
+          for (int k = 0; k < ptr[r0 + r + 1] - ptr[r0 + r]; ++k) {
+            col[base + 32 * (size_t)k + r] = (int)I.node + adj[ptr[r0 + r] + k];
+            if (fem) val[base + 32 * (size_t)k + r] = off_val[ptr[r0 + r] + k];
+          }
+        if (base > (size_t)std::numeric_limits<int>::max()) return fail(MREG_ERR_OOM, "operator layout too large");
+        sl.push_back(mreg::SellSlice{p, r0, (int)base, w | (rows << 16)});
+      }
+    }
+    void* m_sl = nullptr;
+    void* m_col = nullptr;
+    void* m_val = nullptr;
+    mreg_status st = b->mem.get(&m_sl, sl.size() * sizeof(mreg::SellSlice), stream);
+    if (!st) st = b->mem.get(&m_col, std::max<size_t>(col.size(), 1) * 4, stream);
+    if (!st && fem) st = b->mem.get(&m_val, std::max<size_t>(val.size(), 1) * 4, stream);
+    if (st) {
+      b->mem.put(m_sl, stream);
+      b->mem.put(m_col, stream);
+      return st;
+    }
+    CK(cudaMemcpyAsync(m_sl, sl.data(), sl.size() * sizeof(mreg::SellSlice),
+                       cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(m_col, col.data(), col.size() * 4, cudaMemcpyHostToDevice, s), "upload");
+    if (fem)
+      CK(cudaMemcpyAsync(m_val, val.data(), val.size() * 4, cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    b->sell_slices = (mreg::SellSlice*)m_sl;
+    b->sell_col = (int*)m_col;
+    b->sell_val = (float*)m_val;
+    b->n_sell_slices = (int)sl.size();
   }
-  CK(mreg::launch_batch_apply_operator(b->form, b->d_args, b->setup.node_off, b->op_tiles,
-                                       b->n_op_tiles, (const float2*)x_dev, (float2*)y_dev,
-                                       b->num_sms, s),
+  CK(mreg::launch_batch_apply_operator(b->form, b->d_args, b->setup.node_off, b->sell_slices,
+                                       b->n_sell_slices, b->sell_col, b->sell_val,
+                                       (const float2*)x_dev, (float2*)y_dev, s),
      "operator kernel launch");
   return MREG_OK;
 }
@@ -262,7 +312,9 @@ void mreg_batch_destroy(mreg_batch* b) {
     if (e) cudaEventDestroy(e);
   b->mem.put(b->part, nullptr);
   b->mem.put(b->epart, nullptr);
-  b->mem.put(b->op_tiles, nullptr);
+  b->mem.put(b->sell_slices, nullptr);
+  b->mem.put(b->sell_col, nullptr);
+  b->mem.put(b->sell_val, nullptr);
   b->mem.put(b->arena, nullptr);
   delete b;
 }

@@ -879,36 +879,42 @@ __device__ __forceinline__ float2 ff_residual(float4 b4, const AxAcc<kFormUmbrel
                      ff_to_f(ff_add(ff{b4.z, b4.w}, ff_neg(A.ay))));
 }
 
-// The solve's starting guess extrapolated from the last two iterates,
-// 2 x - p (the same FP32 expression wherever a node's value is formed).
-__device__ __forceinline__ float2 cheb_extrapolate(float2 x, float2 p) {
-  return make_float2(__fmaf_rn(2.0f, x.x, -p.x), __fmaf_rn(2.0f, x.y, -p.y));
+// The solve's starting guess: the polynomial extrapolation of the last
+// iterates x (u_k), p (u_{k-1}) and q (u_{k-2}) to the next one, of degree
+// nh = the earlier iterates held: x, 2 x - p, or 3 (x - p) + q (the same
+// FP32 expression wherever a node's value is formed).
+__device__ __forceinline__ float2 cheb_guess(float2 x, float2 p, float2 q, int nh) {
+  if (nh == 0) return x;
+  if (nh == 1) return make_float2(__fmaf_rn(2.0f, x.x, -p.x), __fmaf_rn(2.0f, x.y, -p.y));
+  return make_float2(__fmaf_rn(3.0f, x.x - p.x, q.x), __fmaf_rn(3.0f, x.y - p.y, q.y));
 }
 
-// (A x)_i and, with p, (A x0)_i for x0 = 2 x - p (x0 = x without p): both
-// gathers in one pass over the node's neighbours.
+// (A x)_i and (A x0)_i for the guess x0 of cheb_guess: both gathers in one
+// pass over the node's neighbours (p, q read when nh says they are held).
 template <int L>
 __device__ __forceinline__ void cheb_ax2(const IterArgs& a, const Topo& T, bool cached,
-                                         const float2* x, const float2* p, int i, float2 xi,
-                                         float2 x0i, int& deg, const NodeLanes<L>& nl,
-                                         AxAcc<kFormUmbrella>& A, AxAcc<kFormUmbrella>& A0) {
+                                         const float2* x, const float2* p, const float2* q, int nh,
+                                         int i, float2 xi, float2 x0i, int& deg,
+                                         const NodeLanes<L>& nl, AxAcc<kFormUmbrella>& A,
+                                         AxAcc<kFormUmbrella>& A0) {
   int beg;
   T.arow(a, cached, i, beg, deg);
   A.init_part(a, i, xi, nl.lead());
   A0.init_part(a, i, x0i, nl.lead());
   for (int k0 = 4 * nl.sub; k0 < deg; k0 += 4 * L) {
-    float2 xj[4], pj[4];
+    float2 xj[4], pj[4], qj[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = (k0 + u < deg) ? T.adj(a, cached, beg, k0 + u) : i;
       xj[u] = x[j];
-      pj[u] = p ? p[j] : xj[u];
+      pj[u] = nh >= 1 ? p[j] : xj[u];
+      qj[u] = nh >= 2 ? q[j] : xj[u];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (k0 + u >= deg) continue;
       A.add(a, beg + k0 + u, xj[u]);
-      A0.add(a, beg + k0 + u, p ? cheb_extrapolate(xj[u], pj[u]) : xj[u]);
+      A0.add(a, beg + k0 + u, cheb_guess(xj[u], pj[u], qj[u], nh));
     }
   }
   nl.sum(A);
@@ -921,20 +927,21 @@ __device__ __forceinline__ void cheb_ax2(const IterArgs& a, const Topo& T, bool 
 // with the spline gradient it was formed with the sample), the residual of
 // the pending solve's iterate against its right-hand side bprev (when one
 // is pending), b = D_m (x - tau F), and the first step of the solve from
-// the starting guess x0 = 2 x - p, p the iterate one iteration earlier (pr;
-// x0 = x without one): r_0 = b - A x0, x_1 = x0 + d_0.  The iterate is
-// saved to pw for the next iteration's guess.  On a smooth trajectory the
-// extrapolated guess is much closer to the solution than x, so fewer steps
-// reach the same residual bound.
+// the starting guess x0 extrapolated from x and the nh iterates before it
+// (pr one iteration earlier, pq two; cheb_guess): r_0 = b - A x0,
+// x_1 = x0 + d_0.  The iterate is saved to pw for the next iterations'
+// guesses.  On a smooth trajectory the extrapolated guess is much closer to
+// the solution than x, so fewer steps reach the same residual bound.
 // acc: ||r_prev||^2 (x, y), ||b||^2 (x, y), ||r_0||^2 (x, y).
 template <int GRAD, int L>
 __device__ __forceinline__ void cheb_start_node(const IterArgs& a, const Topo& T, bool cached,
                                                 const float2* x, float2* xn, float2* dd,
                                                 const float4* bprev, float4* bnew, float2* F,
-                                                const float2* pr, float2* pw,
-                                                int i, float* acc, const NodeLanes<L>& nl) {
+                                                const float2* pr, const float2* pq, int nh,
+                                                float2* pw, int i, float* acc,
+                                                const NodeLanes<L>& nl) {
   const float2 xi = x[i];
-  const float2 x0i = pr ? cheb_extrapolate(xi, pr[i]) : xi;
+  const float2 x0i = cheb_guess(xi, nh >= 1 ? pr[i] : xi, nh >= 2 ? pq[i] : xi, nh);
   float2 Fi;
   if (GRAD == 1) {
     Fi = F[i];
@@ -945,7 +952,7 @@ __device__ __forceinline__ void cheb_start_node(const IterArgs& a, const Topo& T
   }
   int deg;
   AxAcc<kFormUmbrella> A, A0;
-  cheb_ax2<L>(a, T, cached, x, pr, i, xi, x0i, deg, nl, A, A0);
+  cheb_ax2<L>(a, T, cached, x, pr, pq, nh, i, xi, x0i, deg, nl, A, A0);
   if (!nl.lead()) return;
   pw[i] = xi;
   if (bprev) {
@@ -1100,11 +1107,12 @@ __device__ __forceinline__ bool run_chebyshev(const IterArgs& a, TEAM& team, uns
   float2* xc = reinterpret_cast<float2*>(a.cg + 2 * (size_t)nV);
   float2* xn = xc + nV;
   float2* const dd = xc + 2 * (size_t)nV;
-  // The iterate at the force phase of each iteration goes to history buffer
-  // (it + prev_guess) & 1; the other buffer holds the previous iteration's
-  // (an earlier launch's last one for it = 0 when prev_guess > 0).
-  float2* const up0 = cheb_history(a.cg, nV, 0);
-  float2* const up1 = cheb_history(a.cg, nV, 1);
+  // The iterate at the force phase of iteration it goes to history buffer
+  // (hist_pos + it) mod 3; the one before it (an earlier launch's, for the
+  // first iterations) is in the buffer behind, and the one before that in
+  // the buffer behind that.
+  float2* const hist[3] = {cheb_history(a.cg, nV, 0), cheb_history(a.cg, nV, 1),
+                           cheb_history(a.cg, nV, 2)};
   int par = 0;   // half of the partial-sum buffer used by the next reduction
 
   for (int i = tid; i < nV; i += nth) xc[i] = a.u[i];
@@ -1132,10 +1140,12 @@ __device__ __forceinline__ bool run_chebyshev(const IterArgs& a, TEAM& team, uns
       float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
       const float4* bprev = pend_it < 0 ? nullptr : ((pend_it & 1) ? bb1 : bb0);
       float4* const bcur = (it & 1) ? bb1 : bb0;
-      const int hp = (it + a.prev_guess) & 1;
-      const float2* pr = (it == 0 && a.prev_guess == 0) ? nullptr : (hp ? up0 : up1);
-      float2* const pw = hp ? up1 : up0;
-      FOR_NODES(i, cached) cheb_start_node<GRAD, L>(a, T, cached, xc, xn, dd, bprev, bcur, F, pr, pw, i, acc, nl);
+      const int wb = (a.hist_pos + it) % 3;
+      const int nh = min(2, a.hist_held + it);
+      float2* const pw = hist[wb];
+      const float2* pr = hist[(wb + 2) % 3];
+      const float2* pq = hist[(wb + 1) % 3];
+      FOR_NODES(i, cached) cheb_start_node<GRAD, L>(a, T, cached, xc, xn, dd, bprev, bcur, F, pr, pq, nh, pw, i, acc, nl);
       block_record<6, false>(acc, ff_zero(), MY_REC, s_red);
       SYNC_OR_LEAVE();
       ff unused;

@@ -43,10 +43,12 @@ struct IterArgs {
   // holding the spectrum of D^-1 A, acosh(theta / delta), and the factor of
   // the a-priori step count (sqrt(max / min of diag A) over a safety margin)
   float cheb_theta, cheb_delta, cheb_acosh, cheb_scale;
-  // S1 by Chebyshev semi-iteration: 0 when no earlier iterate is held, else
-  // 1 + the history buffer (cheb_history) holding the iterate one iteration
-  // before u, from which the first solve of the launch extrapolates its guess
-  int prev_guess;
+  // S1 by Chebyshev semi-iteration: the iterates before u held in the
+  // history buffers (0-2: u_{k-1}, u_{k-2}), from which the launch's first
+  // solves extrapolate their guesses, and the buffer that iteration 0
+  // writes (u_{k-1} is in buffer hist_pos + 2, u_{k-2} in hist_pos + 1,
+  // mod 3)
+  int hist_held, hist_pos;
   float2 tau_ff, lam_ff;   // tau and lambda as float-float pairs {hi, lo}
   // read-only mesh / operator data
   const float2* V;
@@ -81,7 +83,7 @@ struct IterArgs {
   float4* cg;            // CG state, 2 parities x nV x 3 float4: {x,z}, {p,r}, {w,s};
                          // the Chebyshev solve keeps its own state in the same
                          // memory (b: 2 x nV float4, x: 2 x nV float2, d: nV float2,
-                         // history: 2 x nV float2)
+                         // history: 3 x nV float2)
   float2* rt;            // true residual (FP32 copy) for restarts
   float4* b;             // right-hand side, float-float {x.hi, x.lo, y.hi, y.lo}
   // reductions / control
@@ -106,10 +108,10 @@ struct IterArgs {
                          // [3] max CG its, [4] not-converged count
 };
 
-// The Chebyshev solve's two history buffers (nV float2 each) in the CG state
-// memory, after its right-hand sides (2 x nV float4) and x, x', d (3 x nV
-// float2): buffer b holds the iterate at the force phase of the iterations of
-// one parity, which the next iteration extrapolates its starting guess from.
+// The Chebyshev solve's three history buffers (nV float2 each) in the CG
+// state memory, after its right-hand sides (2 x nV float4) and x, x', d
+// (3 x nV float2): a ring of the iterates at the force phases of the last
+// iterations, which the next ones extrapolate their starting guesses from.
 __host__ __device__ inline float2* cheb_history(float4* cg, int nV, int b) {
   return reinterpret_cast<float2*>(cg + 2 * (size_t)nV) + (3 + (size_t)b) * nV;
 }
@@ -196,15 +198,20 @@ cudaError_t launch_warp_grad(const WarpArgs& a, int grid, float2* rg, float2* tp
                              float2* grad_out, cudaStream_t s);
 
 // y = A x with the semi-implicit system matrix of form (S1, or S2 with the
-// stored entries); x, y: nV float2.  Batched: packed x, y over the pairs,
-// blocks of operator_tile_nodes() nodes of one pair each (tiles: (pair,
-// first node)).
+// stored entries); x, y: nV float2.
 cudaError_t launch_apply_operator(int form, const IterArgs& a, const float2* x, float2* y,
                                   int num_sms, cudaStream_t s);
+// Batched: the pairs' rows in sliced-ELLPACK form (SellSlice records: slices
+// of 32 consecutive rows of one pair; entry k of the slice's row r at
+// col[off + 32 k + r], as a packed node index, -1 past the row's end; val
+// the matching S2 off-diagonal entries, unused for S1).
+struct SellSlice {
+  int pair, row0, off, wr;   // wr: slice width | rows << 16
+};
 cudaError_t launch_batch_apply_operator(int form, const IterArgs* args, const int* node_off,
-                                        const int2* tiles, int n_tiles, const float2* x,
-                                        float2* y, int num_sms, cudaStream_t s);
-int operator_tile_nodes();
+                                        const SellSlice* slices, int n_slices, const int* col,
+                                        const float* val, const float2* x, float2* y,
+                                        cudaStream_t s);
 
 // Iteration kernel: occupancy query and cooperative launch.
 // The data term and the regulariser of Eq. 1 at a.u into out[0], out[1]

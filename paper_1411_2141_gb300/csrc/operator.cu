@@ -120,20 +120,91 @@ __global__ void __launch_bounds__(kOpBlock) k_apply(const Op a, const float2* __
     apply_rows<FORM>(a, x, y, t0 + (int)threadIdx.x, kOpBlock);
 }
 
-// Batched: block t handles the kOpTile nodes from tiles[t].y of pair
-// tiles[t].x; x and y are packed over the pairs (pair p from node_off[p]).
-// (A persistent grid looping over the tiles, with the pair's operator
-// reloaded only when the pair changes, measured no faster on GB300.)
+// Batched, sliced ELLPACK: a warp takes kSellWarpSlices slices of 32 rows,
+// lane r row r of each; entry k of every row of a slice is one warp-wide
+// load (col[off + 32 k + lane]), so the column indices arrive coalesced and
+// without a row-pointer load in front of them, and the x gathers of all of
+// a thread's rows are issued together.  Entries are summed in the row's
+// ascending order with the same fused multiply-adds as apply_rows, so the
+// result is bitwise the one-pair product's.
+constexpr int kSellWarpSlices = 2;
+
 template <int FORM>
-__global__ void __launch_bounds__(kOpBlock) k_batch_apply(const IterArgs* __restrict__ args,
-                                                         const int* __restrict__ node_off,
-                                                         const int2* __restrict__ tiles,
-                                                         const float2* __restrict__ x,
-                                                         float2* __restrict__ y) {
-  const int2 t = __ldg(tiles + blockIdx.x);
-  const Op a = op_of(args[t.x]);
-  const int off = __ldg(node_off + t.x);
-  apply_rows<FORM>(a, x + off, y + off, t.y + (int)threadIdx.x, kOpBlock);
+__global__ void __launch_bounds__(kOpBlock)
+k_batch_apply(const IterArgs* __restrict__ args, const int* __restrict__ node_off,
+              const SellSlice* __restrict__ slices, int n_slices, const int* __restrict__ col,
+              const float* __restrict__ val, const float2* __restrict__ x, float2* __restrict__ y) {
+  constexpr int S = kSellWarpSlices;
+  const int lane = threadIdx.x & 31;
+  const int first = (blockIdx.x * (kOpBlock / 32) + (threadIdx.x >> 5)) * S;
+  int off[S], w[S], gi[S], lr[S], pr[S];
+  bool on[S];
+  int longest = 0;
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    const bool ok = first + r < n_slices;
+    const SellSlice sl = ok ? slices[first + r] : SellSlice{0, 0, 0, 0};
+    off[r] = sl.off;
+    w[r] = sl.wr & 0xffff;
+    on[r] = lane < (sl.wr >> 16);
+    pr[r] = sl.pair;
+    lr[r] = sl.row0 + lane;
+    gi[r] = (ok ? __ldg(node_off + sl.pair) : 0) + lr[r];
+    longest = max(longest, w[r]);
+  }
+  float sx[S], sy[S];
+  int deg[S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    sx[r] = 0.0f;
+    sy[r] = 0.0f;
+    deg[r] = 0;
+  }
+  for (int k0 = 0; k0 < longest; k0 += kOpGather) {
+    int j[S][kOpGather];
+    float a[S][kOpGather];
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+#pragma unroll
+      for (int u = 0; u < kOpGather; ++u) {
+        const int k = k0 + u;
+        const bool ok = k < w[r];
+        j[r][u] = ok ? __ldg(col + off[r] + 32 * k + lane) : -1;
+        a[r][u] = (FORM == kFormUmbrella || !ok) ? 1.0f : __ldg(val + off[r] + 32 * k + lane);
+      }
+    }
+    float2 v[S][kOpGather];
+#pragma unroll
+    for (int r = 0; r < S; ++r)
+#pragma unroll
+      for (int u = 0; u < kOpGather; ++u)
+        v[r][u] = j[r][u] >= 0 ? __ldg(x + j[r][u]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+#pragma unroll
+      for (int u = 0; u < kOpGather; ++u) {
+        if (j[r][u] < 0) continue;
+        ++deg[r];
+        sx[r] = __fmaf_rn(a[r][u], v[r][u].x, sx[r]);
+        sy[r] = __fmaf_rn(a[r][u], v[r][u].y, sy[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    if (!on[r]) continue;
+    const float2 xi = __ldg(x + gi[r]);
+    float2 out;
+    if (FORM == kFormUmbrella) {
+      const float lam = args[pr[r]].lam;
+      const float d = (1.0f + lam) * (float)deg[r];
+      out = make_float2(__fmaf_rn(-lam, sx[r], d * xi.x), __fmaf_rn(-lam, sy[r], d * xi.y));
+    } else {
+      const float d = __ldg(args[pr[r]].Adiag + lr[r]);
+      out = make_float2(__fmaf_rn(d, xi.x, sx[r]), __fmaf_rn(d, xi.y, sy[r]));
+    }
+    y[gi[r]] = out;
+  }
 }
 
 }  // namespace
@@ -147,17 +218,19 @@ cudaError_t launch_apply_operator(int form, const IterArgs& a, const float2* x, 
 }
 
 cudaError_t launch_batch_apply_operator(int form, const IterArgs* args, const int* node_off,
-                                        const int2* tiles, int n_tiles, const float2* x,
-                                        float2* y, int num_sms, cudaStream_t s) {
-  if (n_tiles <= 0) return cudaSuccess;
-  (void)num_sms;
+                                        const SellSlice* slices, int n_slices, const int* col,
+                                        const float* val, const float2* x, float2* y,
+                                        cudaStream_t s) {
+  if (n_slices <= 0) return cudaSuccess;
+  const int per_block = (kOpBlock / 32) * kSellWarpSlices;
+  const int grid = (n_slices + per_block - 1) / per_block;
   if (form == kFormUmbrella)
-    k_batch_apply<kFormUmbrella><<<n_tiles, kOpBlock, 0, s>>>(args, node_off, tiles, x, y);
+    k_batch_apply<kFormUmbrella><<<grid, kOpBlock, 0, s>>>(args, node_off, slices, n_slices, col,
+                                                         val, x, y);
   else
-    k_batch_apply<kFormFemNodes><<<n_tiles, kOpBlock, 0, s>>>(args, node_off, tiles, x, y);
+    k_batch_apply<kFormFemNodes><<<grid, kOpBlock, 0, s>>>(args, node_off, slices, n_slices, col,
+                                                         val, x, y);
   return cudaGetLastError();
 }
-
-int operator_tile_nodes() { return kOpTile; }
 
 }  // namespace mreg

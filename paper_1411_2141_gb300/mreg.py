@@ -150,7 +150,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mreg_energy_terms": ([vp, C.POINTER(dbl), C.POINTER(dbl), vp], i32),
         "mreg_get_u": ([vp, vp, i32, vp], i32),
         "mreg_set_u": ([vp, vp, i32, vp], i32),
-        "mreg_set_u_prev": ([vp, vp, i32, vp], i32),
+        "mreg_set_u_prev": ([vp, vp, i32, i32, vp], i32),
         "mreg_get_field": ([vp, i32, vp, i32, C.POINTER(i64), vp], i32),
         "mreg_stats": ([vp, C.POINTER(mreg_stats_t), vp], i32),
         "mreg_destroy": ([vp], None),
@@ -459,19 +459,24 @@ class Registration:
         _check(load().mreg_set_u(self._h, a.ctypes.data, 0, _stream_ptr(stream)), "mreg_set_u")
 
     def set_u_prev(self, u_prev, stream=None):
-        """The iterate one iteration before u for the Chebyshev solve's
-        extrapolated guess (None drops it); call after set_u."""
-        if u_prev is None:
-            _check(load().mreg_set_u_prev(self._h, None, 0, _stream_ptr(stream)), "mreg_set_u_prev")
-            return
-        if _is_torch_cuda(u_prev):
-            _check(load().mreg_set_u_prev(self._h, u_prev.data_ptr(), 1, _stream_ptr(stream)),
+        """The iterates before u for the Chebyshev solve's extrapolated guess,
+        (n_prev, n_nodes, 2) newest first as get_field(MREG_FIELD_U_PREV)
+        returns them (None or n_prev = 0 drops them); call after set_u."""
+        if u_prev is None or u_prev.shape[0] == 0:
+            _check(load().mreg_set_u_prev(self._h, None, 0, 0, _stream_ptr(stream)),
                    "mreg_set_u_prev")
             return
+        if tuple(u_prev.shape[1:]) != (self.n_nodes, 2):
+            raise ValueError("u_prev must be (n_prev, n_nodes, 2)")
+        n_prev = int(u_prev.shape[0])
+        if _is_torch_cuda(u_prev):
+            if not u_prev.is_contiguous():
+                raise ValueError("u_prev must be contiguous")
+            _check(load().mreg_set_u_prev(self._h, u_prev.data_ptr(), n_prev, 1,
+                                          _stream_ptr(stream)), "mreg_set_u_prev")
+            return
         a = np.ascontiguousarray(u_prev, dtype=np.float32)
-        if a.shape != (self.n_nodes, 2):
-            raise ValueError("u_prev must be (n_nodes, 2)")
-        _check(load().mreg_set_u_prev(self._h, a.ctypes.data, 0, _stream_ptr(stream)),
+        _check(load().mreg_set_u_prev(self._h, a.ctypes.data, n_prev, 0, _stream_ptr(stream)),
                "mreg_set_u_prev")
 
     def get_field(self, field: int, stream=None) -> np.ndarray:
@@ -486,8 +491,10 @@ class Registration:
         if n.value:
             _check(lib.mreg_get_field(self._h, field, out.ctypes.data, 0, None, _stream_ptr(stream)),
                    "mreg_get_field")
-        if field in (MREG_FIELD_U, MREG_FIELD_FORCE, MREG_FIELD_U_PREV):
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
             out = out.reshape(-1, 2)
+        elif field == MREG_FIELD_U_PREV:
+            out = out.reshape(-1, self.n_nodes, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
                 field == MREG_FIELD_COEF_TE_16 and n.value):
             out = out.reshape(self.height, self.width)
@@ -626,7 +633,7 @@ class Batch:
         if n.value:
             _check(lib.mreg_batch_get_field(self._h, int(pair), field, out.ctypes.data, 0, None,
                                             _stream_ptr(stream)), "mreg_batch_get_field")
-        if field in (MREG_FIELD_U, MREG_FIELD_FORCE, MREG_FIELD_U_PREV):
+        if field in (MREG_FIELD_U, MREG_FIELD_FORCE):
             out = out.reshape(-1, 2)
         elif field in (MREG_FIELD_COEF_RE, MREG_FIELD_COEF_TE, MREG_FIELD_PIXEL_TRI) or (
                 field == MREG_FIELD_COEF_TE_16 and n.value):

@@ -99,6 +99,6 @@ def test_launch_counts_match_the_measured_launch_lists():
 
 
 def test_operator_bytes():
-    # S1: row pointers, columns, x and y; S2 adds the stored values and diagonal
-    assert bench.operator_bytes(10, 60, "S1") == 4 * 11 + 4 * 60 + 16 * 10
+    # S1: columns, x and y; S2 adds the stored values and diagonal
+    assert bench.operator_bytes(10, 60, "S1") == 4 * 60 + 16 * 10
     assert bench.operator_bytes(10, 60, "S2") == bench.operator_bytes(10, 60, "S1") + 4 * 60 + 40

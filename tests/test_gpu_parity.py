@@ -217,22 +217,24 @@ def test_runs_are_bitwise_repeatable(mreg, c0):
 def test_checkpoint_resume_is_bitwise(mreg, c0, mode):
     """A registration stopped after 10 iterations and resumed from a
     checkpoint of its state continues bit for bit as the uninterrupted one:
-    the state is u and, for the Chebyshev solve of S1, the iterate one
-    iteration earlier that its next starting guess is extrapolated from.
-    Ten plus ten iterations in two calls on one handle match too."""
+    the state is u and, for the Chebyshev solve of S1, the two iterates
+    before it that its next starting guess is extrapolated from.  Ten plus
+    ten iterations in two calls on one handle match too, and so do 1 + 1 +
+    18 (the history grows from none to two across calls)."""
     with _reg(mreg, c0, mode) as r:
         r.step(20)
         u20 = r.get_u()
-    with _reg(mreg, c0, mode) as r:
-        r.step(10)
-        r.step(10)
-        assert np.array_equal(r.get_u(), u20)
+    for split in ((10, 10), (1, 1, 18)):
+        with _reg(mreg, c0, mode) as r:
+            for n in split:
+                r.step(n)
+            assert np.array_equal(r.get_u(), u20), split
     with _reg(mreg, c0, mode) as r:
         assert r.get_field(mreg.MREG_FIELD_U_PREV).size == 0
         r.step(10)
         u10, p10 = r.get_u(), r.get_field(mreg.MREG_FIELD_U_PREV)
     held = mode == "S1"
-    assert p10.shape == ((c0.n_nodes, 2) if held else (0, 2))
+    assert p10.shape == ((2, c0.n_nodes, 2) if held else (0, c0.n_nodes, 2))
     with _reg(mreg, c0, mode) as r:
         r.set_u(u10)
         if held:
@@ -242,23 +244,29 @@ def test_checkpoint_resume_is_bitwise(mreg, c0, mode):
         assert np.array_equal(r.get_u(), u20)
 
 
-def test_previous_iterate_is_dropped_with_the_iterate(mreg, c0):
-    """set_u and reset drop the held previous iterate (the next solve starts
-    from u itself); set_u_prev checks its handle and its values."""
+def test_previous_iterates_are_dropped_with_the_iterate(mreg, c0):
+    """The history holds the iterates before u, newest first, growing to two;
+    set_u and reset drop it (the next solve starts from u itself, then
+    extrapolates linearly); set_u_prev checks its handle and values."""
     with _reg(mreg, c0, "S1") as r:
-        r.step(3)
+        r.step(1)
+        u1 = r.get_u()
+        assert r.get_field(mreg.MREG_FIELD_U_PREV).shape == (1, c0.n_nodes, 2)
+        r.step(1)
+        h = r.get_field(mreg.MREG_FIELD_U_PREV)
+        assert h.shape == (2, c0.n_nodes, 2)
+        assert np.array_equal(h[0], u1) and np.abs(h[1]).max() == 0.0   # u_1, then u_0 = 0
         u3 = r.get_u()
-        assert r.get_field(mreg.MREG_FIELD_U_PREV).shape == (c0.n_nodes, 2)
         r.set_u(u3)
         assert r.get_field(mreg.MREG_FIELD_U_PREV).size == 0
         r.step(2)
         r.reset()
         assert r.get_field(mreg.MREG_FIELD_U_PREV).size == 0
-        r.step(1)
+        r.step(3)
         r.set_u_prev(None)
         assert r.get_field(mreg.MREG_FIELD_U_PREV).size == 0
-        bad = np.zeros((c0.n_nodes, 2), np.float32)
-        bad[5, 1] = np.inf
+        bad = np.zeros((1, c0.n_nodes, 2), np.float32)
+        bad[0, 5, 1] = np.inf
         with pytest.raises(mreg.MregError):
             r.set_u_prev(bad)
         # the first solve after set_u starts from u: a fresh handle given the
@@ -272,7 +280,7 @@ def test_previous_iterate_is_dropped_with_the_iterate(mreg, c0):
         assert np.array_equal(r.get_u(), a)
     with _reg(mreg, c0, "S0") as r:
         with pytest.raises(mreg.MregError):
-            r.set_u_prev(np.zeros((c0.n_nodes, 2), np.float32))
+            r.set_u_prev(np.zeros((1, c0.n_nodes, 2), np.float32))
 
 
 def test_reset_restarts_the_registration(mreg, c0):
