@@ -8,8 +8,9 @@
 namespace mreg {
 namespace {
 
-// DIR 0: rows, DIR 1: columns; one warp per task (a window of 96 floats in
-// registers per lane: at most 128 registers, four blocks per SM).
+// DIR 0: rows, DIR 1: columns; one warp per task (columns: a window of 96
+// floats in registers per lane, at most 128 registers; rows: the window in
+// shared memory, 12.7 KB per warp; four blocks per SM either way).
 template <int DIR>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
 k_prefilter(const float* __restrict__ in, int64_t in_stride, float* __restrict__ out,

@@ -9,17 +9,18 @@
 // One warp filters 32 lines (rows, then columns) over one segment of kSegLen
 // outputs.  The causal recursion c+(n) = 6 s(n) + z1 c+(n-1) and the
 // anticausal recursion c-(n) = z1 (c-(n+1) - c+(n)) run lane-per-line over a
-// window of the line's mirror-symmetric extension held in registers, which
-// extends kWarm samples beyond the segment on each side: the states
-// entering the window are taken as 0, whose effect decays as
-// |z1|^kWarm ~ 7e-10, below FP32 resolution.  Reading the mirror extension
-// at the image border makes the windowed recursion the mirror-boundary
-// prefilter itself (Unser's exact initial values are the infinite
-// recursions over that extension), so every window is handled alike.  All
-// of a lane's window loads are independent and issued together.  Columns
-// are read directly (consecutive lanes, consecutive addresses); rows are
-// staged transposed through shared memory so that the global loads and
-// stores stay warp-wide and the lane-per-line accesses conflict-free.
+// window of the line's mirror-symmetric extension, which extends kWarm
+// samples beyond the segment on each side: the states entering the window
+// are taken as 0, whose effect decays as |z1|^kWarm ~ 7e-10, below FP32
+// resolution.  Reading the mirror extension at the image border makes the
+// windowed recursion the mirror-boundary prefilter itself (Unser's exact
+// initial values are the infinite recursions over that extension), so
+// every window is handled alike.  All of a lane's window loads are
+// independent and issued together.  Columns are read directly (consecutive
+// lanes, consecutive addresses) into registers; rows are staged transposed
+// into shared memory by asynchronous copies, so that the global loads and
+// stores stay warp-wide and the lane-per-line accesses conflict-free, and
+// filtered there in place.
 //
 // Pixel map (set-up of step a4): every pixel centre gets the smallest-index
 // closed triangle of the undeformed mesh that contains it.  The inside test
@@ -60,19 +61,60 @@ __device__ __forceinline__ int mirror_index(int j, int N) {
   return j < N ? j : p - j;
 }
 
-// The two recursions over one window held in registers, v = gain * samples:
-// causal c+(k) = v(k) + z1 c+(k-1) from a zero state before the window,
-// then anticausal c(k) = z1 (c(k+1) - c+(k)) from a zero state after it,
-// down to the first output (kWarm).  The zero states stand in for the
-// line's samples beyond the window; their effect on the outputs decays as
-// |z1|^kWarm ~ 7e-10 (relative to the samples), below FP32 resolution.
+// The two recursions over one window, v = gain * samples: causal
+// c+(k) = v(k) + z1 c+(k-1) (one fused multiply-add) from a zero state
+// before the window, then anticausal c(k) = z1 (c(k+1) - c+(k)) from a zero
+// state after it, down to the first output (kWarm).  The zero states stand
+// in for the line's samples beyond the window; their effect on the outputs
+// decays as |z1|^kWarm ~ 7e-10 (relative to the samples), below FP32
+// resolution.  Every operation is rounded as written (explicit intrinsics:
+// no contraction left to the compiler), so the register form and the
+// shared-memory form give the same bits.
+__device__ __forceinline__ float prefilter_causal(float z, float prev, float v) {
+  return __fmaf_rn(z, prev, v);
+}
+__device__ __forceinline__ float prefilter_anticausal(float z, float next, float cp) {
+  return __fmul_rn(z, __fsub_rn(next, cp));
+}
+
+// ... over a window held in registers
 __device__ __forceinline__ void prefilter_window(float (&v)[kWin]) {
   const float z = kZ1;
 #pragma unroll
-  for (int k = 1; k < kWin; ++k) v[k] = __fmaf_rn(z, v[k - 1], v[k]);
-  v[kWin - 1] = -z * v[kWin - 1];
+  for (int k = 1; k < kWin; ++k) v[k] = prefilter_causal(z, v[k - 1], v[k]);
+  v[kWin - 1] = prefilter_anticausal(z, 0.0f, v[kWin - 1]);
 #pragma unroll
-  for (int k = kWin - 2; k >= kWarm; --k) v[k] = z * (v[k + 1] - v[k]);
+  for (int k = kWin - 2; k >= kWarm; --k) v[k] = prefilter_anticausal(z, v[k + 1], v[k]);
+}
+
+// ... over a window in shared memory (t: the lane's line, stride kPitch),
+// in place: a handful of instructions in rolled loops
+__device__ __forceinline__ void prefilter_window_shared(float* t) {
+  const float z = kZ1;
+  float c = t[0];
+#pragma unroll 4
+  for (int k = 1; k < kWin; ++k) {
+    c = prefilter_causal(z, c, t[k * kPitch]);
+    t[k * kPitch] = c;
+  }
+  c = prefilter_anticausal(z, 0.0f, c);
+  t[(kWin - 1) * kPitch] = c;
+#pragma unroll 4
+  for (int k = kWin - 2; k >= kWarm; --k) {
+    c = prefilter_anticausal(z, c, t[k * kPitch]);
+    t[k * kPitch] = c;
+  }
+}
+
+// 4-byte asynchronous copy global -> shared (cp.async, through L1).
+__device__ __forceinline__ void copy_async_4(float* dst_shared, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+  unsigned long long g;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Number of warp tasks (32 lines x one segment) of one pass.
@@ -105,36 +147,30 @@ __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int
   const int nl = min(32, nlines - line0);
   const int on = min(kSegLen, N - s0);
   const float gain = 6.0f;
-  float v[kWin];
 
   if (DIR == 0) {
-    // stage: the loads of 16 lines (three warp-wide loads each) are issued
-    // before their transposed shared-memory stores
+    // stage: every sample of the window is copied asynchronously into the
+    // transposed tile (tile[k * kPitch + l]: sample k of line l), all of the
+    // warp's copies in flight together and no registers held for them;
+    // then each lane runs both recursions over its line in place
     int col[kWin / 32];
 #pragma unroll
     for (int j = 0; j < kWin / 32; ++j) col[j] = mirror_index(w0 + lane + 32 * j, N);
+#pragma unroll 4
+    for (int l = 0; l < nl; ++l) {
+      const float* src = in + (int64_t)(line0 + l) * in_stride;
 #pragma unroll
-    for (int l0 = 0; l0 < 32; l0 += 16) {
-      float r[16][kWin / 32];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int l = l0 + q;
-        const float* src = in + (int64_t)(line0 + (l < nl ? l : 0)) * in_stride;
-#pragma unroll
-        for (int j = 0; j < kWin / 32; ++j) r[q][j] = l < nl ? __ldg(src + col[j]) : 0.0f;
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-#pragma unroll
-        for (int j = 0; j < kWin / 32; ++j) tile[(lane + 32 * j) * kPitch + l0 + q] = gain * r[q][j];
+      for (int j = 0; j < kWin / 32; ++j)
+        copy_async_4(tile + (lane + 32 * j) * kPitch + l, src + col[j]);
     }
+    copy_async_wait_all();
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < kWin; ++k) v[k] = tile[k * kPitch + lane];
-    prefilter_window(v);
-    __syncwarp();   // every lane has read the window before outputs overwrite it
-#pragma unroll
-    for (int k = 0; k < kSegLen; ++k) tile[k * kPitch + lane] = v[kWarm + k];
+    if (lane < nl) {
+      float* t = tile + lane;
+#pragma unroll 8
+      for (int k = 0; k < kWin; ++k) t[k * kPitch] = __fmul_rn(gain, t[k * kPitch]);
+      prefilter_window_shared(t);
+    }
     __syncwarp();
     // write the segment: each row's outputs as warp-wide stores
     for (int l = 0; l < nl; ++l) {
@@ -142,15 +178,16 @@ __device__ __forceinline__ void prefilter_task(const float* __restrict__ in, int
 #pragma unroll
       for (int j = 0; j < kSegLen / 32; ++j) {
         const int k = lane + 32 * j;
-        if (k < on) dst[k] = tile[k * kPitch + l];
+        if (k < on) dst[k] = tile[(kWarm + k) * kPitch + l];
       }
     }
   } else {
     if (lane >= nl) return;   // no warp-wide operation follows
+    float v[kWin];
     const float* src = in + line0 + lane;
 #pragma unroll
     for (int k = 0; k < kWin; ++k)
-      v[k] = gain * __ldg(src + (int64_t)mirror_index(w0 + k, N) * in_stride);
+      v[k] = __fmul_rn(gain, __ldg(src + (int64_t)mirror_index(w0 + k, N) * in_stride));
     prefilter_window(v);
     float* dst = out + (int64_t)s0 * out_stride + line0 + lane;
 #pragma unroll
