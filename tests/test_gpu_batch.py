@@ -160,12 +160,13 @@ def test_two_ctas_per_sm_register_budget(mreg, small, oracle_small, mode, grad):
 
 
 def test_fields_of_a_pair(mreg, small):
-    from oracle import bspline
+    from oracle import bspline, register
     with _batch(mreg, small[:3], mode="S1", coeff_bf16=True) as b:
         b.run(3)
         for k, case in enumerate(small[:3]):
             pix = b.get_field(k, mreg.MREG_FIELD_PIXEL_TRI)
-            assert pix.shape == case.Re.shape and pix.min() >= 0 and pix.max() < case.n_tris
+            H, W = case.Re.shape
+            assert np.array_equal(pix, register.locate_pixels(case.V, case.T, W, H).astype(np.int32))
             c = bspline.prefilter_2d(case.Te.astype(np.float64))
             cg = b.get_field(k, mreg.MREG_FIELD_COEF_TE)
             assert np.abs(cg - c).max() <= 5e-6 * np.abs(c).max()

@@ -101,9 +101,39 @@ def test_prefilter_config0(mreg, c0):
     assert np.abs(got - ref).max() <= 5e-6 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("which", ["c0", (37, 53), (130, 70), (2, 2)])
+def _grid_case(n=8, h=4, seed=3):
+    """A mesh with every node on a pixel centre: the grid lines and the
+    diagonals of its triangles pass through pixel centres, so many centres
+    lie on edges and corners shared by several closed triangles."""
+    side = n * h + 1
+    g = np.arange(n + 1) * h
+    V = np.array([(x, y) for y in g for x in g], np.float32)
+    T = []
+    for j in range(n):
+        for i in range(n):
+            a = j * (n + 1) + i
+            b, c = a + 1, a + n + 1
+            d = c + 1
+            T += [(a, b, d), (a, d, c)] if (i + j) % 2 == 0 else [(a, b, c), (b, d, c)]
+    rng = np.random.default_rng(seed)
+    Re = rng.normal(size=(side, side)).astype(np.float32)
+    Te = rng.normal(size=(side, side)).astype(np.float32)
+    spec = inputs.CaseSpec(side=side, n_nodes=len(V), seed=seed)
+    return inputs.Case(spec=spec, Re=Re, Te=Te, V=V, T=np.array(T, np.int32),
+                       d=np.zeros((side, side, 2)))
+
+
+@pytest.mark.parametrize("which", ["c0", (37, 53), (130, 70), (2, 2), "grid"])
 def test_pixel_map_bit_exact(mreg, c0, which):
-    case = c0 if which == "c0" else _ragged_case(*which, seed=7)
+    """The owner of every pixel centre, against the oracle's exhaustive
+    search: the smallest-index closed triangle that contains it (the grid
+    mesh puts centres on shared edges and corners)."""
+    if which == "c0":
+        case = c0
+    elif which == "grid":
+        case = _grid_case()
+    else:
+        case = _ragged_case(*which, seed=7)
     with _reg(mreg, case) as r:
         got = r.get_field(mreg.MREG_FIELD_PIXEL_TRI)
     H, W = case.Re.shape
