@@ -977,6 +977,25 @@ __device__ __forceinline__ void cheb_start_node(const IterArgs& a, const Topo& T
   xn[i] = make_float2(x0i.x + d.x, x0i.y + d.y);
 }
 
+// The update of one step at node i from its (A x)_i: r = b - A x,
+// d = c_r D^-1 r (+ c_d d_prev), x' = x + d; every operation rounded as
+// written.  Returns x'.
+__device__ __forceinline__ float2 cheb_update(const IterArgs& a, int i, const AxAcc<kFormUmbrella>& A,
+                                              float2 xi, const float4* b, float2* xn, float2* dd,
+                                              ChebStep s, bool first) {
+  const float2 r = ff_residual(b[i], A);
+  const float di = __ldg(a.dinv + i);
+  float2 d = make_float2(__fmul_rn(s.c_r, __fmul_rn(di, r.x)), __fmul_rn(s.c_r, __fmul_rn(di, r.y)));
+  if (!first) {
+    const float2 dp = dd[i];
+    d = make_float2(__fmaf_rn(s.c_d, dp.x, d.x), __fmaf_rn(s.c_d, dp.y, d.y));
+  }
+  dd[i] = d;
+  const float2 x1 = make_float2(__fadd_rn(xi.x, d.x), __fadd_rn(xi.y, d.y));
+  xn[i] = x1;
+  return x1;
+}
+
 // One step at node i (x -> xn); with SAMPLE also Te at the new iterate:
 // f, the energy term into e and (spline gradient) the force into Fs.
 template <int GRAD, int L, bool SAMPLE>
@@ -988,20 +1007,74 @@ __device__ __forceinline__ void cheb_step_node(const IterArgs& a, const Topo& T,
   int deg;
   const AxAcc<kFormUmbrella> A = cheb_ax<L>(a, T, cached, x, i, xi, deg, nl);
   if (!nl.lead()) return;
-  const float2 r = ff_residual(b[i], A);
-  const float di = __ldg(a.dinv + i);
-  float2 d = make_float2(s.c_r * (di * r.x), s.c_r * (di * r.y));
-  if (!first) {
-    const float2 dp = dd[i];
-    d = make_float2(__fmaf_rn(s.c_d, dp.x, d.x), __fmaf_rn(s.c_d, dp.y, d.y));
-  }
-  dd[i] = d;
-  const float2 x1 = make_float2(xi.x + d.x, xi.y + d.y);
-  xn[i] = x1;
+  const float2 x1 = cheb_update(a, i, A, xi, b, xn, dd, s, first);
   if (SAMPLE) {
     float2 unusedF;
     e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, i, x1, a.f + i, Fs + i, &unusedF));
   }
+}
+
+// The same step at two nodes i and j of the thread whose topology is not
+// cached (rows read from global memory): both nodes' row bounds, then both
+// neighbour gathers, are issued together, so the two dependent load chains
+// overlap instead of running one after the other.  Each node's sums run in
+// the same order as in cheb_step_node, so the results are bitwise the same.
+template <int GRAD, int L, bool SAMPLE>
+__device__ __forceinline__ void cheb_step_node2(const IterArgs& a, const Topo& T,
+                                                const float2* x, float2* xn, float2* dd,
+                                                const float4* b, int i, int j, ChebStep s,
+                                                bool first, float2* Fs, ff& e,
+                                                const NodeLanes<L>& nl) {
+  const float2 xi = x[i], xj = x[j];
+  int bi, di, bj, dj;
+  T.arow(a, false, i, bi, di);
+  T.arow(a, false, j, bj, dj);
+  AxAcc<kFormUmbrella> A, B;
+  A.init_part(a, i, xi, nl.lead());
+  B.init_part(a, j, xj, nl.lead());
+  const int dm = max(di, dj);
+  for (int k0 = 4 * nl.sub; k0 < dm; k0 += 4 * L) {
+    float2 vi[4], vj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      vi[u] = (k0 + u < di) ? x[__ldg(a.adj_col + bi + k0 + u)] : make_float2(0.0f, 0.0f);
+      vj[u] = (k0 + u < dj) ? x[__ldg(a.adj_col + bj + k0 + u)] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u < di) A.add(a, bi + k0 + u, vi[u]);
+      if (k0 + u < dj) B.add(a, bj + k0 + u, vj[u]);
+    }
+  }
+  nl.sum(A);
+  nl.sum(B);
+  A.finish(a, di, xi);
+  B.finish(a, dj, xj);
+  if (!nl.lead()) return;
+  const float2 x1 = cheb_update(a, i, A, xi, b, xn, dd, s, first);
+  const float2 y1 = cheb_update(a, j, B, xj, b, xn, dd, s, first);
+  if (SAMPLE) {
+    float2 unusedF;
+    e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, i, x1, a.f + i, Fs + i, &unusedF));
+    e = ff_add_f(e, sample_node<kFormUmbrella, GRAD>(a, j, y1, a.f + j, Fs + j, &unusedF));
+  }
+}
+
+// A step over all of the thread's nodes in the node loop's order: the first
+// (cached topology) alone, the others two at a time.
+template <int GRAD, int L, bool SAMPLE>
+__device__ __forceinline__ void cheb_step_nodes(const IterArgs& a, const Topo& T,
+                                                const float2* x, float2* xn, float2* dd,
+                                                const float4* b, ChebStep s, bool first,
+                                                float2* Fs, ff& e, const NodeLanes<L>& nl,
+                                                int ntid, int nnth) {
+  const int nV = a.nV;
+  int i = ntid;
+  if (i >= nV) return;
+  cheb_step_node<GRAD, L, SAMPLE>(a, T, true, x, xn, dd, b, i, s, first, Fs, e, nl);
+  for (i += nnth; i + nnth < nV; i += 2 * nnth)
+    cheb_step_node2<GRAD, L, SAMPLE>(a, T, x, xn, dd, b, i, i + nnth, s, first, Fs, e, nl);
+  if (i < nV) cheb_step_node<GRAD, L, SAMPLE>(a, T, false, x, xn, dd, b, i, s, first, Fs, e, nl);
 }
 
 // Residual of the iterate x against b at node i: acc += ||b - A x||^2 (x, y).
@@ -1071,9 +1144,9 @@ __device__ __forceinline__ bool cheb_steps(const IterArgs& a, TEAM& team, const 
     const ChebStep s = f0 ? seq.first(a) : seq.next(a);
     ff e = ff_zero();
     if (j + 1 < n) {
-      FOR_NODES(i, cached) cheb_step_node<GRAD, L, false>(a, T, cached, xc, xn, dd, b, i, s, f0, Fs, e, nl);
+      cheb_step_nodes<GRAD, L, false>(a, T, xc, xn, dd, b, s, f0, Fs, e, nl, ntid, nnth);
     } else {
-      FOR_NODES(i, cached) cheb_step_node<GRAD, L, true>(a, T, cached, xc, xn, dd, b, i, s, f0, Fs, e, nl);
+      cheb_step_nodes<GRAD, L, true>(a, T, xc, xn, dd, b, s, f0, Fs, e, nl, ntid, nnth);
       warp_energy_store(e, eslot, gwarp);
     }
     if (!team.sync_local()) return false;
