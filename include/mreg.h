@@ -552,8 +552,16 @@ mreg_status mreg_batch_stats(mreg_batch* b, int32_t pair, mreg_stats_t* out, voi
 
 /* mreg_apply_operator for every pair of the batch in one launch: x_dev and
  * y_dev hold n_nodes x 2 floats of every pair, packed in pair order (pair p
- * starts at the sum of the node counts of the pairs before it).  The first
- * call allocates 8 bytes per 256 nodes of block table.  Asynchronous.      */
+ * starts at the sum of the node counts of the pairs before it); y_dev must
+ * not be x_dev.  The first call copies the pairs' matrices back from the
+ * device once and lays their rows out in sliced-ELLPACK form (slices of 32
+ * consecutive rows of one pair, each padded to its longest row; for S2 also
+ * the entries' values), in memory from the batch's allocator that is
+ * released with the batch, and blocks; later calls are asynchronous.  Each
+ * row's entries are summed in the same order, with the same operations, as
+ * by mreg_apply_operator, so the results are bitwise the same.  Errors:
+ * INVALID_ARG for NULL pointers, x_dev == y_dev or the explicit mode (no
+ * system matrix); OOM; CUDA.                                               */
 mreg_status mreg_batch_apply_operator(mreg_batch* b, const float* x_dev, float* y_dev,
                                       void* stream);
 
